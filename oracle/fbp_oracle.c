@@ -1,0 +1,237 @@
+/*
+ * FP64 CPU oracle for parallel-beam filtered backprojection (FBP).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The GPU library
+ * shares no code, header, table or constant with it.
+ *
+ * It is plain and slow on purpose: every function is the definition it cites,
+ * written out with explicit loops in double precision, no blocking and no
+ * reordering.  Paper: "Performance evaluation in the reconstruction of 2D
+ * images of computed tomography using massively parallel programming CUDA"
+ * (arXiv 2109.02174).
+ *
+ * Conventions (the paper fixes none of them; these are the readings used by
+ * the whole project):
+ *   - pixel (row r, column c) of an n x n image has centre
+ *       x = c - (n-1)/2,  y = r - (n-1)/2            (pixel size 1)
+ *   - detector bin k of n_det bins has centre t_k = (k - (n_det-1)/2) * tau
+ *   - a ray at angle theta is the line x cos(theta) + y sin(theta) = t
+ *     (section "Computed tomography", the line equation before Eq. 2)
+ *   - the filtered projection is read between bins by linear interpolation
+ *     with zero outside [0, n_det)
+ *   - Eq. 2 sums over the angles; the angular step pi/n_angles is applied so
+ *     that the result approximates the attenuation density.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+enum { ORACLE_RAM_LAK = 0, ORACLE_SHEPP_LOGAN = 1, ORACLE_NONE = 2 };
+
+/*
+ * Spatial filter taps H (the convolution kernel of Q = P * H, text after
+ * Eq. 2).  The paper does not name H; the band-limited ramp kernels of
+ * Kak & Slaney ("Principles of Computerized Tomographic Imaging", ch. 3) are
+ * used:
+ *   Ram-Lak:     h(0) = 1/(4 tau^2), h(m) = 0 for even m != 0,
+ *                h(m) = -1/(pi^2 m^2 tau^2) for odd m
+ *   Shepp-Logan: h(m) = 2 / (pi^2 tau^2 (1 - 4 m^2))
+ *   none:        h(0) = 1/tau, else 0   (so that Q = P)
+ * Output: h[m + n_det - 1] = h(m) for m = -(n_det-1) .. n_det-1
+ * (2*n_det - 1 values).  Returns 0, or -1 on a bad argument.
+ */
+int oracle_taps(int kind, int n_det, double tau, double *h)
+{
+    if (n_det < 1 || !(tau > 0.0) || h == NULL) return -1;
+    for (int m = -(n_det - 1); m <= n_det - 1; ++m) {
+        double v;
+        if (kind == ORACLE_RAM_LAK) {
+            if (m == 0)
+                v = 1.0 / (4.0 * tau * tau);
+            else if (m % 2 == 0)
+                v = 0.0;
+            else
+                v = -1.0 / (M_PI * M_PI * (double)m * (double)m * tau * tau);
+        } else if (kind == ORACLE_SHEPP_LOGAN) {
+            v = 2.0 / (M_PI * M_PI * tau * tau * (1.0 - 4.0 * (double)m * (double)m));
+        } else if (kind == ORACLE_NONE) {
+            v = (m == 0) ? 1.0 / tau : 0.0;
+        } else {
+            return -1;
+        }
+        h[m + n_det - 1] = v;
+    }
+    return 0;
+}
+
+/*
+ * Filtered projections Q_theta = P_theta * H (text after Eq. 2), as the
+ * discrete linear convolution of each sinogram row with the taps, the row
+ * being zero outside the detector:
+ *   Q[i][k] = tau * sum_{j=0}^{n_det-1} h(k - j) * P[i][j],   k in [0, n_det)
+ * P has row stride ld (>= n_det); Q has row stride n_det.
+ */
+void oracle_filter(const double *P, int n_angles, int n_det, int ld,
+                   const double *h, double tau, double *Q)
+{
+    for (int i = 0; i < n_angles; ++i) {
+        for (int k = 0; k < n_det; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < n_det; ++j)
+                s += h[(k - j) + n_det - 1] * P[(size_t)i * ld + j];
+            Q[(size_t)i * n_det + k] = tau * s;
+        }
+    }
+}
+
+/* Q_i read at fractional bin u: linear interpolation, zero outside [0,n_det). */
+static double interp(const double *q, int n_det, double u)
+{
+    double fk = floor(u);
+    double w = u - fk;
+    long k = (long)fk;
+    double q0 = (k >= 0 && k < n_det) ? q[k] : 0.0;
+    double q1 = (k + 1 >= 0 && k + 1 < n_det) ? q[k + 1] : 0.0;
+    return (1.0 - w) * q0 + w * q1;
+}
+
+/*
+ * One pixel of Eq. 2: f(x,y) = (pi/n_angles) * sum_i Q_i(x cos th_i + y sin th_i),
+ * the angles summed in order i = 0 .. n_angles-1.
+ */
+static double pixel_value(const double *Q, int n_angles, int n_det,
+                          const double *theta, double tau, int n, int r, int c)
+{
+    double x = (double)c - 0.5 * (double)(n - 1);
+    double y = (double)r - 0.5 * (double)(n - 1);
+    double s = 0.0;
+    for (int i = 0; i < n_angles; ++i) {
+        double t = x * cos(theta[i]) + y * sin(theta[i]);
+        double u = t / tau + 0.5 * (double)(n_det - 1);
+        s += interp(Q + (size_t)i * n_det, n_det, u);
+    }
+    return s * (M_PI / (double)n_angles);
+}
+
+typedef struct {
+    const double *Q;
+    const double *theta;
+    double tau;
+    double *f;
+    int n_angles, n_det, n, r0, r1;
+} bp_job;
+
+static void *bp_rows(void *arg)
+{
+    bp_job *j = (bp_job *)arg;
+    for (int r = j->r0; r < j->r1; ++r)
+        for (int c = 0; c < j->n; ++c)
+            j->f[(size_t)r * j->n + c] =
+                pixel_value(j->Q, j->n_angles, j->n_det, j->theta, j->tau, j->n, r, c);
+    return NULL;
+}
+
+/*
+ * Backprojection (Eq. 2) of filtered rows Q [n_angles][n_det] into the image
+ * f [n][n] (row-major, f[r][c]).  nthreads > 1 splits the image rows over
+ * POSIX threads; every pixel is computed the same way whatever the split.
+ */
+void oracle_backproject(const double *Q, int n_angles, int n_det,
+                        const double *theta, double tau, int n, double *f,
+                        int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n) nthreads = n;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    bp_job *jobs = (bp_job *)malloc(sizeof(bp_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].Q = Q;
+        jobs[t].theta = theta;
+        jobs[t].tau = tau;
+        jobs[t].f = f;
+        jobs[t].n_angles = n_angles;
+        jobs[t].n_det = n_det;
+        jobs[t].n = n;
+        jobs[t].r0 = (int)((long)n * t / nthreads);
+        jobs[t].r1 = (int)((long)n * (t + 1) / nthreads);
+    }
+    if (nthreads == 1) {
+        bp_rows(&jobs[0]);
+    } else {
+        for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, bp_rows, &jobs[t]);
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    }
+    free(jobs);
+    free(th);
+}
+
+/* Eq. 2 at selected pixels only (for spot checks of large images). */
+void oracle_backproject_pixels(const double *Q, int n_angles, int n_det,
+                               const double *theta, double tau, int n,
+                               const int *rows, const int *cols, int count,
+                               double *out)
+{
+    for (int p = 0; p < count; ++p)
+        out[p] = pixel_value(Q, n_angles, n_det, theta, tau, n, rows[p], cols[p]);
+}
+
+/*
+ * Discrete projection of an image (the Radon transform of the section
+ * "Computed tomography", Fig. 1) in the form that is the exact transpose of
+ * the interpolation above: each pixel adds its value to the two bins around
+ * its detector coordinate with the linear-interpolation weights,
+ *   P[i][k] = sum_{pixels} f(x,y) * max(0, 1 - |u_i(x,y) - k|),
+ * with u_i(x,y) = (x cos th_i + y sin th_i)/tau + (n_det-1)/2 and the pi/n_angles
+ * factor left out.  P is [n_angles][n_det].
+ */
+void oracle_forward(const double *f, int n, int n_angles, int n_det,
+                    const double *theta, double tau, double *P)
+{
+    memset(P, 0, sizeof(double) * (size_t)n_angles * (size_t)n_det);
+    for (int i = 0; i < n_angles; ++i) {
+        double *p = P + (size_t)i * n_det;
+        for (int r = 0; r < n; ++r) {
+            for (int c = 0; c < n; ++c) {
+                double x = (double)c - 0.5 * (double)(n - 1);
+                double y = (double)r - 0.5 * (double)(n - 1);
+                double t = x * cos(theta[i]) + y * sin(theta[i]);
+                double u = t / tau + 0.5 * (double)(n_det - 1);
+                double fk = floor(u);
+                double w = u - fk;
+                long k = (long)fk;
+                double v = f[(size_t)r * n + c];
+                if (k >= 0 && k < n_det) p[k] += (1.0 - w) * v;
+                if (k + 1 >= 0 && k + 1 < n_det) p[k + 1] += w * v;
+            }
+        }
+    }
+}
+
+/*
+ * Whole FBP: taps, row filter, backprojection.  P has row stride ld.
+ * Returns 0, or -1 on a bad argument or allocation failure.
+ */
+int oracle_fbp(const double *P, int n_angles, int n_det, int ld,
+               const double *theta, double tau, int kind, int n, double *f,
+               int nthreads)
+{
+    if (n_angles < 1 || n_det < 1 || n < 1 || ld < n_det) return -1;
+    double *h = (double *)malloc(sizeof(double) * (size_t)(2 * n_det - 1));
+    double *Q = (double *)malloc(sizeof(double) * (size_t)n_angles * (size_t)n_det);
+    if (h == NULL || Q == NULL || oracle_taps(kind, n_det, tau, h) != 0) {
+        free(h);
+        free(Q);
+        return -1;
+    }
+    oracle_filter(P, n_angles, n_det, ld, h, tau, Q);
+    oracle_backproject(Q, n_angles, n_det, theta, tau, n, f, nthreads);
+    free(h);
+    free(Q);
+    return 0;
+}
