@@ -1,0 +1,169 @@
+/*
+ * fbp.h -- C ABI of libfbp: GPU filtered backprojection (FBP) for 2D
+ * parallel-beam CT on NVIDIA GB300 (sm_103a).
+ *
+ * The method is the paper's Eq. 2 ("Performance evaluation in the
+ * reconstruction of 2D images of computed tomography using massively parallel
+ * programming CUDA", arXiv 2109.02174, section "Computed tomography"):
+ *
+ *     f(x,y) = (pi/A) * sum_{i=0}^{A-1} Q_i(x cos th_i + y sin th_i),
+ *     Q_i    = P_i * H   (each sinogram row convolved with a ramp filter)
+ *
+ * Geometry (the paper fixes none of it; this library's convention):
+ *   - image f is n_pix x n_pix, row-major f[r][c]; pixel centre
+ *     x = c - (n_pix-1)/2, y = r - (n_pix-1)/2 (pixel size 1);
+ *   - detector bin k of n_det has centre t_k = (k - (n_det-1)/2) * det_spacing;
+ *   - Q_i is read at t by linear interpolation, zero outside [0, n_det);
+ *   - the angular weight pi/A is applied (Eq. 2 as printed omits it).
+ *
+ * Conventions of every call:
+ *   - Ownership: the caller owns every buffer passed in (device memory unless
+ *     stated); the plan owns its own tables.  Nothing here frees caller memory.
+ *   - Asynchrony: compute calls only enqueue work on `stream` and return; the
+ *     result is ready when the stream is.  fbp_plan() synchronises once (table
+ *     upload).  A NULL stream is the legacy default stream.
+ *   - Errors: every call returns an fbp_status; fbp_last_error() gives a
+ *     message for the calling thread.  Arguments are checked on the host
+ *     before any launch.  A device-side timeout (a bounded wait that ran out)
+ *     is recorded in the plan's status word: fbp_device_status() reads it.
+ *   - Alignment: every device pointer must be 16-byte aligned, else
+ *     FBP_ERR_ALIGNMENT.
+ *   - Element type: float for FBP_F32 plans, double for FBP_F64 plans (the
+ *     sinogram, the image and, unless q_storage says otherwise, the filtered
+ *     sinogram).
+ */
+#ifndef FBP_H
+#define FBP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque plan: geometry, filter, trig and filter tables, tuned launch shape. */
+typedef struct fbp_plan_s *fbp_plan_t;
+
+/* A CUDA stream (the same type as cudaStream_t). */
+typedef struct CUstream_st *fbp_stream_t;
+
+typedef enum {
+    FBP_OK = 0,
+    FBP_ERR_INVALID_ARG = 1,
+    FBP_ERR_ALIGNMENT = 2,
+    FBP_ERR_OUT_OF_MEMORY = 3,
+    FBP_ERR_BUDGET = 4,
+    FBP_ERR_CUDA = 5,
+    FBP_ERR_TIMEOUT = 6,
+    FBP_ERR_UNSUPPORTED = 7
+} fbp_status;
+
+/* The filter H of Q = P * H.  The paper does not name it; the band-limited
+ * spatial ramp kernels of Kak & Slaney (ch. 3) are offered:
+ *   Ram-Lak:     h(0) = 1/(4 tau^2), h(m even) = 0, h(m odd) = -1/(pi^2 m^2 tau^2)
+ *   Shepp-Logan: h(m) = 2/(pi^2 tau^2 (1 - 4 m^2))
+ *   none:        Q = P (plain backprojection)
+ * and Q_i[k] = tau * sum_{j=0}^{n_det-1} h(k-j) P_i[j] (linear convolution). */
+typedef enum {
+    FBP_FILTER_RAM_LAK = 0,
+    FBP_FILTER_SHEPP_LOGAN = 1,
+    FBP_FILTER_NONE = 2
+} fbp_filter_type;
+
+/* Element types. */
+enum { FBP_F32 = 0, FBP_F64 = 1, FBP_F16 = 2 };
+/* Accumulation over angles: plain FP32 sum, or Kahan-compensated. */
+enum { FBP_ACC_PLAIN = 0, FBP_ACC_KAHAN = 1 };
+/* Filter route (all compute the same linear convolution). */
+enum { FBP_PATH_AUTO = 0, FBP_PATH_TOEPLITZ_TC = 1, FBP_PATH_FFT = 2, FBP_PATH_DIRECT = 3 };
+
+typedef struct {
+    int dtype;        /* FBP_F32 (default) or FBP_F64 (float-vs-double comparison) */
+    int q_storage;    /* FBP_F32 (default) or FBP_F16: element type of the filtered sinogram */
+    int accumulate;   /* FBP_ACC_PLAIN (default) or FBP_ACC_KAHAN */
+    int filter_path;  /* FBP_PATH_AUTO (default), _TOEPLITZ_TC, _FFT or _DIRECT */
+    int fft_len;      /* 0 = auto (next power of two >= 2*n_det-1) */
+    int tile_x;       /* 0 = auto; pixel tile of one backprojection work item */
+    int tile_y;       /* 0 = auto */
+    int angle_chunk;  /* 0 = auto; angles staged per shared-memory window */
+} fbp_options;
+
+/* Fill *opt with the defaults listed above. */
+fbp_status fbp_options_default(fbp_options *opt);
+
+/*
+ * Create a plan on the current CUDA device.
+ *   n_pix        image side, 1 .. 16384
+ *   n_angles     projections, 1 .. 65535
+ *   n_det        detector bins per projection, 1 .. 65535
+ *   angles       host array of n_angles radians (copied), or NULL for
+ *                th_i = i*pi/n_angles
+ *   det_spacing  bin width tau in pixel units, > 0
+ *   filter       fbp_filter_type
+ *   opt          NULL for defaults
+ * Errors: FBP_ERR_INVALID_ARG (bad size, non-finite angle, tau <= 0),
+ * FBP_ERR_UNSUPPORTED (option combination not built), FBP_ERR_OUT_OF_MEMORY,
+ * FBP_ERR_CUDA.  On error *out is NULL.
+ */
+fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det,
+                    const double *angles, double det_spacing,
+                    fbp_filter_type filter, const fbp_options *opt);
+
+/* Release the plan's device tables (synchronises the device). NULL is a no-op. */
+fbp_status fbp_plan_destroy(fbp_plan_t plan);
+
+/* Bytes of device workspace fbp_reconstruct() needs (the filtered sinogram). */
+fbp_status fbp_workspace_bytes(fbp_plan_t plan, size_t *bytes);
+
+/* Resolved choices: row pitch (elements) of the filtered sinogram, FFT length
+ * (0 when the FFT route is not used) and filter route.  Any pointer may be NULL. */
+fbp_status fbp_plan_query(fbp_plan_t plan, int *q_pitch, int *fft_len, int *filter_path);
+
+/*
+ * Ramp filter, Q = P * H (the text after Eq. 2).
+ *   sino      device [n_angles][ld_sino] of the plan's dtype, ld_sino >= n_det
+ *   filtered  device [n_angles][q_pitch] of q_storage type; bins n_det .. q_pitch-1
+ *             of every row are written as zero
+ */
+fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filtered,
+                      fbp_stream_t stream);
+
+/*
+ * Backprojection, Eq. 2: image[r][c] = (pi/A) sum_i lerp(Q_i, u_i(r,c)) with
+ * u_i = (x cos th_i + y sin th_i)/tau + (n_det-1)/2, angles summed in order
+ * i = 0..A-1 (deterministic: same bits every run).
+ *   filtered  device [n_angles][q_pitch] as written by fbp_filter
+ *   image     device [n_pix][n_pix] of the plan's dtype, written once
+ */
+fbp_status fbp_backproject(fbp_plan_t plan, const void *filtered, void *image,
+                           fbp_stream_t stream);
+
+/*
+ * fbp_filter followed by fbp_backproject, the filtered sinogram kept in
+ * `workspace` (device, >= fbp_workspace_bytes, 16-byte aligned).
+ */
+fbp_status fbp_reconstruct(fbp_plan_t plan, const void *sino, int ld_sino, void *image,
+                           void *workspace, fbp_stream_t stream);
+
+/*
+ * Test-only discrete projector: the exact transpose of the unfiltered
+ * backprojection without its pi/A factor,
+ *   sino[i][k] = sum_{r,c} image[r][c] * max(0, 1 - |u_i(r,c) - k|),
+ * (the projection of section "Computed tomography", Fig. 1).
+ *   image  device [n_pix][n_pix] float (F32 plans only)
+ *   sino   device [n_angles][n_det] float
+ */
+fbp_status radon_forward(fbp_plan_t plan, const void *image, void *sino, fbp_stream_t stream);
+
+/* Read and clear the plan's device status word (synchronises the device):
+ * FBP_OK, or FBP_ERR_TIMEOUT if a bounded device wait ran out since the last read. */
+fbp_status fbp_device_status(fbp_plan_t plan);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *fbp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBP_H */

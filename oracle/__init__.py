@@ -10,7 +10,7 @@ loops).  This wrapper only builds it with gcc and marshals numpy arrays.
 
 Functions (each cites the passage it follows in the C source):
   taps(kind, n_det, tau)                      filter H of Q = P * H
-  filter_rows(P, kind, tau)                   Q[i][k] = tau sum_j h(k-j) P[i][j]
+  filter_rows(P, kind, tau, nthreads)         Q[i][k] = tau sum_j h(k-j) P[i][j]
   backproject(Q, theta, tau, n, nthreads)     Eq. 2 with the pi/A step
   backproject_pixels(Q, theta, tau, n, r, c)  Eq. 2 at selected pixels
   forward(f, theta, n_det, tau)               transpose of the interpolation
@@ -60,6 +60,8 @@ def _load():
             lib.oracle_taps.restype = i
             lib.oracle_filter.argtypes = [d, i, i, i, d, ctypes.c_double, d]
             lib.oracle_filter.restype = None
+            lib.oracle_filter_mt.argtypes = [d, i, i, i, d, ctypes.c_double, d, i]
+            lib.oracle_filter_mt.restype = None
             lib.oracle_backproject.argtypes = [d, i, i, d, ctypes.c_double, i, d, i]
             lib.oracle_backproject.restype = None
             lib.oracle_backproject_pixels.argtypes = [d, i, i, d, ctypes.c_double, i, ip, ip, i, d]
@@ -97,12 +99,15 @@ def taps(kind: int, n_det: int, tau: float = 1.0) -> np.ndarray:
     return h
 
 
-def filter_rows(P, kind: int, tau: float = 1.0) -> np.ndarray:
+def filter_rows(P, kind: int, tau: float = 1.0, nthreads: int = 1) -> np.ndarray:
     P = _f64(P)
     A, D = P.shape
     h = taps(kind, D, tau)
     Q = np.empty((A, D), dtype=np.float64)
-    _load().oracle_filter(_dp(P), A, D, D, _dp(h), float(tau), _dp(Q))
+    if nthreads == 1:
+        _load().oracle_filter(_dp(P), A, D, D, _dp(h), float(tau), _dp(Q))
+    else:
+        _load().oracle_filter_mt(_dp(P), A, D, D, _dp(h), float(tau), _dp(Q), int(nthreads))
     return Q
 
 

@@ -77,17 +77,62 @@ int oracle_taps(int kind, int n_det, double tau, double *h)
  *   Q[i][k] = tau * sum_{j=0}^{n_det-1} h(k - j) * P[i][j],   k in [0, n_det)
  * P has row stride ld (>= n_det); Q has row stride n_det.
  */
-void oracle_filter(const double *P, int n_angles, int n_det, int ld,
-                   const double *h, double tau, double *Q)
+static void filter_row(const double *p, int n_det, const double *h, double tau, double *q)
 {
-    for (int i = 0; i < n_angles; ++i) {
-        for (int k = 0; k < n_det; ++k) {
-            double s = 0.0;
-            for (int j = 0; j < n_det; ++j)
-                s += h[(k - j) + n_det - 1] * P[(size_t)i * ld + j];
-            Q[(size_t)i * n_det + k] = tau * s;
-        }
+    for (int k = 0; k < n_det; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < n_det; ++j) s += h[(k - j) + n_det - 1] * p[j];
+        q[k] = tau * s;
     }
+}
+
+typedef struct {
+    const double *P, *h;
+    double tau;
+    double *Q;
+    int n_det, ld, i0, i1;
+} filt_job;
+
+static void *filter_rows_job(void *arg)
+{
+    filt_job *j = (filt_job *)arg;
+    for (int i = j->i0; i < j->i1; ++i)
+        filter_row(j->P + (size_t)i * j->ld, j->n_det, j->h, j->tau, j->Q + (size_t)i * j->n_det);
+    return NULL;
+}
+
+/* nthreads > 1 splits the rows over POSIX threads (each row is independent). */
+void oracle_filter_mt(const double *P, int n_angles, int n_det, int ld, const double *h,
+                      double tau, double *Q, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n_angles) nthreads = n_angles;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    filt_job *jobs = (filt_job *)malloc(sizeof(filt_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].P = P;
+        jobs[t].h = h;
+        jobs[t].tau = tau;
+        jobs[t].Q = Q;
+        jobs[t].n_det = n_det;
+        jobs[t].ld = ld;
+        jobs[t].i0 = (int)((long)n_angles * t / nthreads);
+        jobs[t].i1 = (int)((long)n_angles * (t + 1) / nthreads);
+    }
+    if (nthreads == 1) {
+        filter_rows_job(&jobs[0]);
+    } else {
+        for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, filter_rows_job, &jobs[t]);
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    }
+    free(jobs);
+    free(th);
+}
+
+void oracle_filter(const double *P, int n_angles, int n_det, int ld, const double *h, double tau,
+                   double *Q)
+{
+    oracle_filter_mt(P, n_angles, n_det, ld, h, tau, Q, 1);
 }
 
 /* Q_i read at fractional bin u: linear interpolation, zero outside [0,n_det). */
@@ -229,7 +274,7 @@ int oracle_fbp(const double *P, int n_angles, int n_det, int ld,
         free(Q);
         return -1;
     }
-    oracle_filter(P, n_angles, n_det, ld, h, tau, Q);
+    oracle_filter_mt(P, n_angles, n_det, ld, h, tau, Q, nthreads);
     oracle_backproject(Q, n_angles, n_det, theta, tau, n, f, nthreads);
     free(h);
     free(Q);

@@ -1,0 +1,238 @@
+"""Python binding of libfbp (include/fbp.h): GPU filtered backprojection on GB300.
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of libfbp.so.  PyTorch supplies device memory and streams.  There is no
+CPU fallback: if libfbp.so is missing or cannot load, every call raises.
+
+Low-level names mirror the C ABI (fbp_plan, fbp_filter, fbp_backproject,
+fbp_reconstruct, radon_forward, ...); ``Plan`` wraps them for tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfbp.so")
+
+FBP_OK, FBP_ERR_INVALID_ARG, FBP_ERR_ALIGNMENT, FBP_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
+FBP_ERR_BUDGET, FBP_ERR_CUDA, FBP_ERR_TIMEOUT, FBP_ERR_UNSUPPORTED = 4, 5, 6, 7
+STATUS_NAMES = {0: "FBP_OK", 1: "FBP_ERR_INVALID_ARG", 2: "FBP_ERR_ALIGNMENT",
+                3: "FBP_ERR_OUT_OF_MEMORY", 4: "FBP_ERR_BUDGET", 5: "FBP_ERR_CUDA",
+                6: "FBP_ERR_TIMEOUT", 7: "FBP_ERR_UNSUPPORTED"}
+FBP_FILTER_RAM_LAK, FBP_FILTER_SHEPP_LOGAN, FBP_FILTER_NONE = 0, 1, 2
+FBP_F32, FBP_F64, FBP_F16 = 0, 1, 2
+FBP_ACC_PLAIN, FBP_ACC_KAHAN = 0, 1
+FBP_PATH_AUTO, FBP_PATH_TOEPLITZ_TC, FBP_PATH_FFT, FBP_PATH_DIRECT = 0, 1, 2, 3
+
+
+class FbpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class fbp_options(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int) for name in
+                ("dtype", "q_storage", "accumulate", "filter_path", "fft_len",
+                 "tile_x", "tile_y", "angle_chunk")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (argtypes); every entry point returns an int status except fbp_last_error.
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "fbp_options_default": [ctypes.POINTER(fbp_options)],
+    "fbp_plan": [ctypes.POINTER(_P), _I, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                 _I, ctypes.POINTER(fbp_options)],
+    "fbp_plan_destroy": [_P],
+    "fbp_workspace_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "fbp_plan_query": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "fbp_filter": [_P, _P, _I, _P, _P],
+    "fbp_backproject": [_P, _P, _P, _P],
+    "fbp_reconstruct": [_P, _P, _I, _P, _P, _P],
+    "radon_forward": [_P, _P, _P, _P],
+    "fbp_device_status": [_P],
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfbp.so (built by ``paper_2109_02174_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise ImportError(f"libfbp.so not found at {path}: run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, argtypes in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = argtypes
+                fn.restype = ctypes.c_int
+            lib.fbp_last_error.argtypes = []
+            lib.fbp_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def fbp_last_error() -> str:
+    return load_library().fbp_last_error().decode()
+
+
+def _check(status: int):
+    if status != FBP_OK:
+        raise FbpError(status, fbp_last_error())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+# ------------------------------------------------------------ raw C-ABI names
+def fbp_options_default() -> fbp_options:
+    o = fbp_options()
+    _check(load_library().fbp_options_default(ctypes.byref(o)))
+    return o
+
+
+def fbp_plan(n_pix, n_angles, n_det, angles=None, det_spacing=1.0, filter=FBP_FILTER_RAM_LAK,
+             opt: fbp_options | None = None) -> int:
+    lib = load_library()
+    h = _P()
+    arr = None
+    if angles is not None:
+        vals = [float(a) for a in angles]
+        arr = (ctypes.c_double * len(vals))(*vals)
+    _check(lib.fbp_plan(ctypes.byref(h), int(n_pix), int(n_angles), int(n_det),
+                        arr, float(det_spacing), int(filter),
+                        ctypes.byref(opt) if opt is not None else None))
+    return h.value
+
+
+def fbp_plan_destroy(plan: int):
+    _check(load_library().fbp_plan_destroy(plan))
+
+
+def fbp_workspace_bytes(plan: int) -> int:
+    v = ctypes.c_size_t()
+    _check(load_library().fbp_workspace_bytes(plan, ctypes.byref(v)))
+    return v.value
+
+
+def fbp_plan_query(plan: int) -> tuple[int, int, int]:
+    a, b, c = _I(), _I(), _I()
+    _check(load_library().fbp_plan_query(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def fbp_filter(plan: int, sino_ptr: int, ld_sino: int, filtered_ptr: int, stream: int):
+    _check(load_library().fbp_filter(plan, sino_ptr, ld_sino, filtered_ptr, stream))
+
+
+def fbp_backproject(plan: int, filtered_ptr: int, image_ptr: int, stream: int):
+    _check(load_library().fbp_backproject(plan, filtered_ptr, image_ptr, stream))
+
+
+def fbp_reconstruct(plan: int, sino_ptr: int, ld_sino: int, image_ptr: int, workspace_ptr: int,
+                    stream: int):
+    _check(load_library().fbp_reconstruct(plan, sino_ptr, ld_sino, image_ptr, workspace_ptr,
+                                          stream))
+
+
+def radon_forward(plan: int, image_ptr: int, sino_ptr: int, stream: int):
+    _check(load_library().radon_forward(plan, image_ptr, sino_ptr, stream))
+
+
+def fbp_device_status(plan: int):
+    _check(load_library().fbp_device_status(plan))
+
+
+# ------------------------------------------------------------ tensor wrapper
+class Plan:
+    """A reconstruction plan bound to torch tensors on the current CUDA device."""
+
+    def __init__(self, n_pix: int, n_angles: int, n_det: int, angles=None,
+                 det_spacing: float = 1.0, filter: int = FBP_FILTER_RAM_LAK, **options):
+        opt = fbp_options_default()
+        for k, v in options.items():
+            setattr(opt, k, int(v))
+        self.n_pix, self.n_angles, self.n_det = int(n_pix), int(n_angles), int(n_det)
+        self.det_spacing = float(det_spacing)
+        self.filter_type = int(filter)
+        self.options = opt
+        self.handle = fbp_plan(n_pix, n_angles, n_det, angles, det_spacing, filter, opt)
+        self.q_pitch, self.fft_len, self.filter_path = fbp_plan_query(self.handle)
+        self.workspace_bytes = fbp_workspace_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fbp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.options.dtype == FBP_F64 else torch.float32
+
+    @property
+    def q_dtype(self):
+        import torch
+        if self.options.q_storage == FBP_F16:
+            return torch.float16
+        return self.dtype
+
+    def empty_filtered(self):
+        import torch
+        return torch.empty((self.n_angles, self.q_pitch), dtype=self.q_dtype, device="cuda")
+
+    def empty_image(self):
+        import torch
+        return torch.empty((self.n_pix, self.n_pix), dtype=self.dtype, device="cuda")
+
+    def empty_workspace(self):
+        import torch
+        return torch.empty(max(self.workspace_bytes, 16), dtype=torch.uint8, device="cuda")
+
+    def filter(self, sino, out=None, stream=None):
+        assert sino.dim() == 2 and sino.shape[0] == self.n_angles and sino.stride(1) == 1
+        out = self.empty_filtered() if out is None else out
+        fbp_filter(self.handle, _ptr(sino), sino.stride(0), _ptr(out), _stream(stream))
+        return out
+
+    def backproject(self, filtered, out=None, stream=None):
+        out = self.empty_image() if out is None else out
+        fbp_backproject(self.handle, _ptr(filtered), _ptr(out), _stream(stream))
+        return out
+
+    def reconstruct(self, sino, out=None, workspace=None, stream=None):
+        assert sino.dim() == 2 and sino.shape[0] == self.n_angles and sino.stride(1) == 1
+        out = self.empty_image() if out is None else out
+        ws = self.empty_workspace() if workspace is None else workspace
+        fbp_reconstruct(self.handle, _ptr(sino), sino.stride(0), _ptr(out), _ptr(ws),
+                        _stream(stream))
+        return out
+
+    def radon_forward(self, image, out=None, stream=None):
+        import torch
+        out = torch.empty((self.n_angles, self.n_det), dtype=torch.float32, device="cuda") \
+            if out is None else out
+        radon_forward(self.handle, _ptr(image), _ptr(out), _stream(stream))
+        return out
+
+    def device_status(self):
+        fbp_device_status(self.handle)

@@ -1,0 +1,386 @@
+// C ABI of libfbp (include/fbp.h): argument checks, plan tables, dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fbp_internal.h"
+
+namespace fbp {
+
+namespace {
+thread_local std::string g_err;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+fbp_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return FBP_ERR_CUDA;
+}
+
+// Common checks of every compute call: plan, device, pointers, alignment.
+fbp_status check_call(const Plan *p, const char *fn, std::initializer_list<const void *> ptrs)
+{
+    if (p == nullptr) {
+        set_error("%s: plan is NULL", fn);
+        return FBP_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) {
+        set_error("%s: plan was made on device %d, current device is %d", fn, p->device, dev);
+        return FBP_ERR_INVALID_ARG;
+    }
+    for (const void *q : ptrs) {
+        if (q == nullptr) {
+            set_error("%s: NULL buffer", fn);
+            return FBP_ERR_INVALID_ARG;
+        }
+        if (!aligned16(q)) {
+            set_error("%s: buffer %p is not 16-byte aligned", fn, q);
+            return FBP_ERR_ALIGNMENT;
+        }
+    }
+    return FBP_OK;
+}
+
+int round_up(int v, int m) { return ((v + m - 1) / m) * m; }
+
+}  // namespace
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+bool encode_q_map(const Plan &p, const void *q, int wraw, CUtensorMap *out)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (enc == nullptr) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return false;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)p.D, (cuuint64_t)p.A};
+    const cuuint64_t strides[1] = {(cuuint64_t)p.pitch * 4u};
+    const cuuint32_t box[2] = {(cuuint32_t)wraw, 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(q), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return false;
+    }
+    return true;
+}
+
+size_t filter_direct_smem_bytes(int D);
+
+}  // namespace fbp
+
+using namespace fbp;
+
+namespace {
+
+void free_plan(Plan *p)
+{
+    if (p == nullptr) return;
+    cudaFree(p->d_trig64);
+    cudaFree(p->d_taps32);
+    cudaFree(p->d_taps64);
+    cudaFree(p->d_status);
+    delete p;
+}
+
+// Spatial taps tau*h(m), m = -(D-1)..D-1 (Kak & Slaney band-limited ramp kernels).
+void make_taps(int kind, int D, double tau, std::vector<double> &out)
+{
+    out.assign((size_t)(2 * D - 1), 0.0);
+    const double pi2 = M_PI * M_PI;
+    for (int m = -(D - 1); m <= D - 1; ++m) {
+        double h;
+        if (kind == FBP_FILTER_RAM_LAK)
+            h = (m == 0) ? 1.0 / (4.0 * tau * tau)
+                         : ((m & 1) ? -1.0 / (pi2 * (double)m * (double)m * tau * tau) : 0.0);
+        else if (kind == FBP_FILTER_SHEPP_LOGAN)
+            h = 2.0 / (pi2 * tau * tau * (1.0 - 4.0 * (double)m * (double)m));
+        else
+            h = (m == 0) ? 1.0 / tau : 0.0;
+        out[(size_t)(m + D - 1)] = tau * h;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+fbp_status fbp_options_default(fbp_options *opt)
+{
+    if (opt == nullptr) {
+        set_error("fbp_options_default: NULL");
+        return FBP_ERR_INVALID_ARG;
+    }
+    std::memset(opt, 0, sizeof *opt);
+    opt->dtype = FBP_F32;
+    opt->q_storage = FBP_F32;
+    opt->accumulate = FBP_ACC_PLAIN;
+    opt->filter_path = FBP_PATH_AUTO;
+    return FBP_OK;
+}
+
+fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const double *angles,
+                    double det_spacing, fbp_filter_type filter, const fbp_options *opt)
+{
+    if (out == nullptr) {
+        set_error("fbp_plan: out is NULL");
+        return FBP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (n_pix < 1 || n_pix > 16384 || n_angles < 1 || n_angles > 65535 || n_det < 1 ||
+        n_det > 65535) {
+        set_error("fbp_plan: sizes out of range (n_pix %d, n_angles %d, n_det %d)", n_pix,
+                  n_angles, n_det);
+        return FBP_ERR_INVALID_ARG;
+    }
+    if (!(det_spacing > 0.0) || !std::isfinite(det_spacing)) {
+        set_error("fbp_plan: det_spacing must be finite and > 0");
+        return FBP_ERR_INVALID_ARG;
+    }
+    if (filter != FBP_FILTER_RAM_LAK && filter != FBP_FILTER_SHEPP_LOGAN &&
+        filter != FBP_FILTER_NONE) {
+        set_error("fbp_plan: unknown filter %d", (int)filter);
+        return FBP_ERR_INVALID_ARG;
+    }
+    fbp_options o;
+    fbp_options_default(&o);
+    if (opt != nullptr) o = *opt;
+    if (o.dtype != FBP_F32) {
+        set_error("fbp_plan: dtype %d not built", o.dtype);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    if (o.q_storage != FBP_F32 || o.accumulate != FBP_ACC_PLAIN) {
+        set_error("fbp_plan: q_storage/accumulate option not built");
+        return FBP_ERR_UNSUPPORTED;
+    }
+    if (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT) {
+        set_error("fbp_plan: filter path %d not built", o.filter_path);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    std::vector<double> theta((size_t)n_angles);
+    for (int i = 0; i < n_angles; ++i) {
+        theta[(size_t)i] = angles ? angles[i] : (double)i * (M_PI / (double)n_angles);
+        if (!std::isfinite(theta[(size_t)i])) {
+            set_error("fbp_plan: angle %d is not finite", i);
+            return FBP_ERR_INVALID_ARG;
+        }
+    }
+
+    Plan *p = new Plan();
+    std::memset(p, 0, sizeof *p);
+    p->n = n_pix;
+    p->A = n_angles;
+    p->D = n_det;
+    p->pitch = round_up(n_det, 8);
+    p->filter = (int)filter;
+    p->dtype = o.dtype;
+    p->q_storage = o.q_storage;
+    p->accumulate = o.accumulate;
+    p->filter_path = FBP_PATH_DIRECT;
+    p->fft_len = 0;
+    p->tau = det_spacing;
+    p->scale64 = M_PI / (double)n_angles;
+    p->scale32 = (float)p->scale64;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        set_error("fbp_plan: no CUDA device");
+        return FBP_ERR_CUDA;
+    }
+
+    std::vector<double2> trig((size_t)n_angles);
+    double ext = 0.0;
+    const int tx = kBpTileX, ty = kBpTileY;
+    for (int i = 0; i < n_angles; ++i) {
+        const double c = std::cos(theta[(size_t)i]) / det_spacing;
+        const double s = std::sin(theta[(size_t)i]) / det_spacing;
+        trig[(size_t)i] = make_double2(c, s);
+        ext = std::fmax(ext, (tx - 1) * std::fabs(c) + (ty - 1) * std::fabs(s));
+    }
+    // The window starts at base >= umin - 5 and must hold bins up to
+    // round(u - base - 1/2) + 1 <= ext + 6, for every pixel u of the tile.
+    const int wraw = round_up((int)std::ceil(ext + 1e-6) + 7, 4);
+    if (wraw > 256) {
+        delete p;
+        set_error("fbp_plan: detector window of %d bins per tile exceeds 256 "
+                  "(det_spacing %.3g too small for the %dx%d tile)", wraw, det_spacing, tx, ty);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    p->bp.tile_x = tx;
+    p->bp.tile_y = ty;
+    p->bp.chunk = kBpChunk;
+    p->bp.wraw = wraw;
+    if (filter_direct_smem_bytes(n_det) > 200 * 1024) {
+        delete p;
+        set_error("fbp_plan: n_det %d too large for the direct filter", n_det);
+        return FBP_ERR_UNSUPPORTED;
+    }
+
+    std::vector<double> taps;
+    make_taps((int)filter, n_det, det_spacing, taps);
+    std::vector<float> taps32(taps.size());
+    for (size_t m = 0; m < taps.size(); ++m) taps32[m] = (float)taps[m];
+
+    cudaError_t e = cudaMalloc(&p->d_trig64, sizeof(double2) * trig.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_taps32, sizeof(float) * taps32.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_taps64, sizeof(double) * taps.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        set_error("fbp_plan: cudaMalloc: %s", cudaGetErrorString(e));
+        return FBP_ERR_OUT_OF_MEMORY;
+    }
+    e = cudaMemcpy(p->d_trig64, trig.data(), sizeof(double2) * trig.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_taps32, taps32.data(), sizeof(float) * taps32.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_taps64, taps.data(), sizeof(double) * taps.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "fbp_plan: table upload");
+    }
+    *out = reinterpret_cast<fbp_plan_t>(p);
+    return FBP_OK;
+}
+
+fbp_status fbp_plan_destroy(fbp_plan_t plan)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (p == nullptr) return FBP_OK;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return FBP_OK;
+}
+
+fbp_status fbp_workspace_bytes(fbp_plan_t plan, size_t *bytes)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (p == nullptr || bytes == nullptr) {
+        set_error("fbp_workspace_bytes: NULL argument");
+        return FBP_ERR_INVALID_ARG;
+    }
+    *bytes = (size_t)p->A * (size_t)p->pitch * sizeof(float);
+    return FBP_OK;
+}
+
+fbp_status fbp_plan_query(fbp_plan_t plan, int *q_pitch, int *fft_len, int *filter_path)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (p == nullptr) {
+        set_error("fbp_plan_query: plan is NULL");
+        return FBP_ERR_INVALID_ARG;
+    }
+    if (q_pitch) *q_pitch = p->pitch;
+    if (fft_len) *fft_len = p->fft_len;
+    if (filter_path) *filter_path = p->filter_path;
+    return FBP_OK;
+}
+
+fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filtered,
+                      fbp_stream_t stream)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    fbp_status st = check_call(p, "fbp_filter", {sino, filtered});
+    if (st != FBP_OK) return st;
+    if (ld_sino < p->D) {
+        set_error("fbp_filter: ld_sino %d < n_det %d", ld_sino, p->D);
+        return FBP_ERR_INVALID_ARG;
+    }
+    cudaError_t e = launch_filter_direct_f32(*p, static_cast<const float *>(sino), ld_sino,
+                                             static_cast<float *>(filtered), stream);
+    return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_filter");
+}
+
+fbp_status fbp_backproject(fbp_plan_t plan, const void *filtered, void *image,
+                           fbp_stream_t stream)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    fbp_status st = check_call(p, "fbp_backproject", {filtered, image});
+    if (st != FBP_OK) return st;
+    CUtensorMap map;
+    if (!encode_q_map(*p, filtered, p->bp.wraw, &map)) return FBP_ERR_CUDA;
+    cudaError_t e = launch_backproject_f32(*p, map, static_cast<float *>(image), stream);
+    return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_backproject");
+}
+
+fbp_status fbp_reconstruct(fbp_plan_t plan, const void *sino, int ld_sino, void *image,
+                           void *workspace, fbp_stream_t stream)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    fbp_status st = check_call(p, "fbp_reconstruct", {sino, image, workspace});
+    if (st != FBP_OK) return st;
+    st = fbp_filter(plan, sino, ld_sino, workspace, stream);
+    if (st != FBP_OK) return st;
+    return fbp_backproject(plan, workspace, image, stream);
+}
+
+fbp_status radon_forward(fbp_plan_t plan, const void *image, void *sino, fbp_stream_t stream)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    fbp_status st = check_call(p, "radon_forward", {image, sino});
+    if (st != FBP_OK) return st;
+    cudaError_t e = launch_radon_forward_f32(*p, static_cast<const float *>(image),
+                                             static_cast<float *>(sino), stream);
+    return e == cudaSuccess ? FBP_OK : cuda_fail(e, "radon_forward");
+}
+
+fbp_status fbp_device_status(fbp_plan_t plan)
+{
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    fbp_status st = check_call(p, "fbp_device_status", {});
+    if (st != FBP_OK) return st;
+    int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "fbp_device_status");
+    if (v != 0) {
+        set_error("device status %d: a bounded device wait ran out", v);
+        return (fbp_status)v;
+    }
+    return FBP_OK;
+}
+
+const char *fbp_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

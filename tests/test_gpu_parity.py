@@ -1,0 +1,235 @@
+"""GPU parity: libfbp (through its C ABI) against the FP64 oracle, element by element.
+
+Bars (FP32 path): max |f_gpu - f_oracle| <= 1e-4 * max|f_oracle| and
+RMSE <= 2e-5 * max|f_oracle|.  Both sides get the same FP32-rounded sinogram.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+MAX_REL = 1e-4
+RMSE_REL = 2e-5
+NTHREADS = 16
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_02174_gb300 import build
+    build.build()
+    import paper_2109_02174_gb300 as m
+    return m
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _np(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def errors(got, ref):
+    scale = float(np.abs(ref).max())
+    return (float(np.abs(got - ref).max()) / scale,
+            float(np.sqrt(np.mean((got - ref) ** 2))) / scale)
+
+
+def assert_parity(got, ref, max_rel=MAX_REL, rmse_rel=RMSE_REL):
+    e_max, e_rms = errors(got, ref)
+    assert e_max <= max_rel and e_rms <= rmse_rel, f"max {e_max:.3e} rmse {e_rms:.3e}"
+
+
+# ---------------------------------------------------------------- filter
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_filter_matches_oracle(fbp, kind):
+    A, D = 37, 211
+    P = np.random.default_rng(20 + kind).standard_normal((A, D)).astype(np.float32)
+    plan = fbp.Plan(150, A, D, filter=kind)
+    q = _np(plan.filter(_t(P)))
+    assert q.shape == (A, plan.q_pitch) and plan.q_pitch % 8 == 0
+    assert np.all(q[:, D:] == 0.0)
+    ref = oracle.filter_rows(P.astype(np.float64), kind, 1.0)
+    np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+def test_filter_respects_row_stride(fbp):
+    import torch
+    A, D = 9, 50
+    big = torch.randn(A, 64, device="cuda")
+    plan = fbp.Plan(30, A, D)
+    q = _np(plan.filter(big[:, :D]))
+    ref = oracle.filter_rows(big[:, :D].double().cpu().numpy(), 0, 1.0)
+    np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- backprojection
+@pytest.mark.parametrize("n,A,D,tau", [
+    (100, 37, 143, 1.0),     # 4x4 tiles with a ragged edge, 3 angle chunks (last partial)
+    (64, 16, 91, 1.0),       # exact tiles, exactly one chunk
+    (33, 50, 60, 0.8),       # one-pixel ragged tile, tau < 1
+    (70, 21, 70, 1.6),       # tau > 1, detector narrower than the diagonal (zero extension)
+])
+def test_backproject_matches_oracle(fbp, n, A, D, tau):
+    rng = np.random.default_rng(n * 7 + A)
+    Q = rng.standard_normal((A, D)).astype(np.float32)
+    th = oracle.default_angles(A)
+    plan = fbp.Plan(n, A, D, det_spacing=tau)
+    qp = np.zeros((A, plan.q_pitch), dtype=np.float32)
+    qp[:, :D] = Q
+    got = _np(plan.backproject(_t(qp)))
+    ref = oracle.backproject(Q.astype(np.float64), th, tau, n, nthreads=NTHREADS)
+    assert_parity(got, ref)
+
+
+def test_backproject_arbitrary_angles(fbp):
+    n, A = 48, 29
+    D = synthetic.det_for(n)
+    rng = np.random.default_rng(99)
+    th = np.sort(rng.uniform(-3.0, 7.0, A))
+    Q = rng.standard_normal((A, D)).astype(np.float32)
+    plan = fbp.Plan(n, A, D, angles=th)
+    qp = np.zeros((A, plan.q_pitch), dtype=np.float32)
+    qp[:, :D] = Q
+    got = _np(plan.backproject(_t(qp)))
+    ref = oracle.backproject(Q.astype(np.float64), th, 1.0, n, nthreads=NTHREADS)
+    assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("n,A,D", [(1, 1, 1), (1, 3, 2), (2, 1, 4), (5, 3, 9), (8, 1, 3)])
+def test_degenerate_sizes(fbp, n, A, D):
+    rng = np.random.default_rng(n + 10 * A + 100 * D)
+    P = rng.standard_normal((A, D)).astype(np.float32)
+    th = oracle.default_angles(A)
+    plan = fbp.Plan(n, A, D, filter=1)
+    got = _np(plan.reconstruct(_t(P)))
+    ref = oracle.fbp(P.astype(np.float64), th, 1.0, 1, n)
+    if np.abs(ref).max() == 0:
+        assert np.all(got == 0)
+    else:
+        assert_parity(got, ref)
+
+
+def test_constant_rows_give_pi_c(fbp):
+    n, A = 64, 45
+    D = synthetic.det_for(n)
+    plan = fbp.Plan(n, A, D)
+    qp = np.zeros((A, plan.q_pitch), dtype=np.float32)
+    qp[:, :D] = 1.25
+    got = _np(plan.backproject(_t(qp)))
+    np.testing.assert_allclose(got, math.pi * 1.25, rtol=2e-6)
+
+
+def test_deterministic_bits(fbp):
+    spec = synthetic.SliceSpec(200, 150, synthetic.det_for(200), 8, seed=31)
+    sino = _t(synthetic.sinogram(spec))
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det)
+    a = _np(plan.reconstruct(sino))
+    b = _np(plan.reconstruct(sino))
+    c = _np(fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det).reconstruct(sino))
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------- whole FBP on the workloads
+def _check_slice(fbp, spec, nthreads=NTHREADS):
+    th = synthetic.default_angles(spec.n_angles)
+    sino32 = synthetic.sinogram(spec, th).astype(np.float32)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
+                    det_spacing=spec.tau)
+    got = _np(plan.reconstruct(_t(sino32)))
+    plan.device_status()
+    ref = oracle.fbp(sino32.astype(np.float64), th, spec.tau, spec.filter, spec.n_pix,
+                     nthreads=nthreads)
+    assert_parity(got, ref)
+    return errors(got, ref)
+
+
+def test_plain_slice_256(fbp):
+    """256x256, 180 angles, 363 bins, Ram-Lak, 10 ellipses (seed 1), noise-free."""
+    _check_slice(fbp, synthetic.cfg_plain())
+
+
+def test_float_slice_512_noisy(fbp):
+    """512x512, 720 angles, 725 bins, Shepp-Logan, Poisson I0 = 1e5 (FP32 path)."""
+    _check_slice(fbp, synthetic.cfg_float_double())
+
+
+def test_large_slice_2048_sampled(fbp):
+    """2048x2048, 2048 angles, 2899 bins: GPU image checked at sampled pixels
+    against the oracle's per-pixel Eq. 2 over the oracle's own filtered rows."""
+    spec = synthetic.cfg_large()
+    th = synthetic.default_angles(spec.n_angles)
+    sino32 = synthetic.sinogram(spec, th).astype(np.float32)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter)
+    got = _np(plan.reconstruct(_t(sino32)))
+    Q = oracle.filter_rows(sino32.astype(np.float64), spec.filter, 1.0, nthreads=NTHREADS)
+    rng = np.random.default_rng(2048)
+    g = np.arange(0, spec.n_pix, 64)
+    gr, gc = np.meshgrid(g, g, indexing="ij")
+    rows = np.concatenate([rng.integers(0, spec.n_pix, 300), gr.ravel(), [0, 2047, 1024, 0, 2047]])
+    cols = np.concatenate([rng.integers(0, spec.n_pix, 300), gc.ravel(), [0, 2047, 1023, 2047, 0]])
+    ref = oracle.backproject_pixels(Q, th, 1.0, spec.n_pix, rows, cols)
+    # max over the sampled oracle values: a lower bound of max|f|, so the bar is stricter
+    scale = float(np.abs(ref).max())
+    err = np.abs(got[rows, cols] - ref) / scale
+    assert err.max() <= MAX_REL and np.sqrt(np.mean(err ** 2)) <= RMSE_REL, \
+        f"max {err.max():.3e} rms {np.sqrt(np.mean(err ** 2)):.3e}"
+
+
+# ---------------------------------------------------------------- projector
+def test_radon_forward_matches_oracle(fbp):
+    n, A = 57, 33
+    D = synthetic.det_for(n)
+    th = oracle.default_angles(A)
+    img = np.random.default_rng(5).random((n, n)).astype(np.float32)
+    plan = fbp.Plan(n, A, D)
+    got = _np(plan.radon_forward(_t(img)))
+    ref = oracle.forward(img.astype(np.float64), th, D)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+def test_gpu_adjoint_pair(fbp):
+    """<R x, y> = (A/pi) <x, B y> for radon_forward and the unfiltered backprojection."""
+    n, A = 80, 40
+    D = synthetic.det_for(n)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((n, n)).astype(np.float32)
+    y = rng.standard_normal((A, D)).astype(np.float32)
+    plan = fbp.Plan(n, A, D, filter=2)
+    yp = np.zeros((A, plan.q_pitch), dtype=np.float32)
+    yp[:, :D] = y
+    Rx = _np(plan.radon_forward(_t(x)))
+    By = _np(plan.backproject(_t(yp)))
+    lhs = float(np.sum(Rx * y))
+    rhs = (A / math.pi) * float(np.sum(x.astype(np.float64) * By))
+    scale = float(np.sum(np.abs(Rx * y)))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+# ---------------------------------------------------------------- errors
+def test_misaligned_and_null_buffers_are_rejected(fbp):
+    import torch
+    plan = fbp.Plan(32, 8, 46)
+    q = torch.zeros(8 * plan.q_pitch + 4, device="cuda")
+    img = torch.zeros(32 * 32 + 4, device="cuda")
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.fbp_backproject(plan.handle, q.data_ptr() + 4, img.data_ptr(), 0)
+    assert e.value.status == fbp.FBP_ERR_ALIGNMENT
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.fbp_backproject(plan.handle, 0, img.data_ptr(), 0)
+    assert e.value.status == fbp.FBP_ERR_INVALID_ARG
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.fbp_filter(plan.handle, q.data_ptr(), 10, img.data_ptr(), 0)
+    assert e.value.status == fbp.FBP_ERR_INVALID_ARG
+    plan.device_status()

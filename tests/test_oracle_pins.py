@@ -254,3 +254,13 @@ def test_fbp_with_detector_spacing():
     xy = (np.arange(n) - 0.5 * (n - 1)) * (2.0 / n)
     X, Y = np.meshgrid(xy, xy)
     assert abs(f[np.hypot(X, Y) < 0.4].mean() - 1.0) < 0.01
+
+
+def test_threaded_filter_and_fbp_match_single_thread():
+    rng = np.random.default_rng(8)
+    P = rng.standard_normal((13, 40))
+    np.testing.assert_array_equal(oracle.filter_rows(P, oracle.RAM_LAK, 1.0, nthreads=4),
+                                  oracle.filter_rows(P, oracle.RAM_LAK, 1.0, nthreads=1))
+    th = oracle.default_angles(13)
+    np.testing.assert_array_equal(oracle.fbp(P, th, 1.0, oracle.SHEPP_LOGAN, 21, nthreads=5),
+                                  oracle.fbp(P, th, 1.0, oracle.SHEPP_LOGAN, 21, nthreads=1))
