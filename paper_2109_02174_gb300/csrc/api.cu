@@ -102,8 +102,6 @@ bool encode_q_map(const Plan &p, const void *q, int wraw, CUtensorMap *out)
     return true;
 }
 
-size_t filter_direct_smem_bytes(int D);
-
 }  // namespace fbp
 
 using namespace fbp;
@@ -116,6 +114,8 @@ void free_plan(Plan *p)
     cudaFree(p->d_trig64);
     cudaFree(p->d_taps32);
     cudaFree(p->d_taps64);
+    cudaFree(p->d_fft_tw);
+    cudaFree(p->d_fft_h);
     cudaFree(p->d_status);
     delete p;
 }
@@ -190,8 +190,30 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         set_error("fbp_plan: q_storage/accumulate option not built");
         return FBP_ERR_UNSUPPORTED;
     }
-    if (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT) {
+    if (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT &&
+        o.filter_path != FBP_PATH_FFT) {
         set_error("fbp_plan: filter path %d not built", o.filter_path);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    // FFT length: any power of two >= 2*n_det - 1 gives the linear convolution.
+    int fft_len = o.fft_len;
+    if (fft_len == 0) {
+        fft_len = 16;
+        while (fft_len < 2 * n_det - 1) fft_len <<= 1;
+    } else if (fft_len < 2 * n_det - 1 || (fft_len & (fft_len - 1)) != 0) {
+        set_error("fbp_plan: fft_len %d must be a power of two >= 2*n_det-1 = %d", fft_len,
+                  2 * n_det - 1);
+        return FBP_ERR_INVALID_ARG;
+    }
+    const bool fft_ok = fft_len <= kMaxFftLen;
+    int path = o.filter_path;
+    if (path == FBP_PATH_AUTO) path = fft_ok ? FBP_PATH_FFT : FBP_PATH_DIRECT;
+    if (path == FBP_PATH_FFT && !fft_ok) {
+        set_error("fbp_plan: FFT length %d exceeds %d", fft_len, kMaxFftLen);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    if (path == FBP_PATH_DIRECT && filter_direct_smem_bytes(n_det) > 200 * 1024) {
+        set_error("fbp_plan: n_det %d too large for the direct filter", n_det);
         return FBP_ERR_UNSUPPORTED;
     }
     std::vector<double> theta((size_t)n_angles);
@@ -213,8 +235,8 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     p->dtype = o.dtype;
     p->q_storage = o.q_storage;
     p->accumulate = o.accumulate;
-    p->filter_path = FBP_PATH_DIRECT;
-    p->fft_len = 0;
+    p->filter_path = path;
+    p->fft_len = (path == FBP_PATH_FFT) ? fft_len : 0;
     p->tau = det_spacing;
     p->scale64 = M_PI / (double)n_angles;
     p->scale32 = (float)p->scale64;
@@ -246,11 +268,6 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     p->bp.tile_y = ty;
     p->bp.chunk = kBpChunk;
     p->bp.wraw = wraw;
-    if (filter_direct_smem_bytes(n_det) > 200 * 1024) {
-        delete p;
-        set_error("fbp_plan: n_det %d too large for the direct filter", n_det);
-        return FBP_ERR_UNSUPPORTED;
-    }
 
     std::vector<double> taps;
     make_taps((int)filter, n_det, det_spacing, taps);
@@ -273,6 +290,30 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_taps64, taps.data(), sizeof(double) * taps.size(),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->filter_path == FBP_PATH_FFT) {
+        const int N = p->fft_len;
+        std::vector<float2> tw((size_t)N);
+        std::vector<double> ct((size_t)N);
+        for (int t = 0; t < N; ++t) {
+            const double a = 2.0 * M_PI * (double)t / (double)N;
+            ct[(size_t)t] = std::cos(a);
+            tw[(size_t)t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+        }
+        // H[f] = sum_m tau h(m) e^{-2 pi i f m / N} = tau h(0) + 2 sum_{m>0} tau h(m) cos(2 pi f m / N)
+        std::vector<float> hs((size_t)N);
+        for (int f = 0; f < N; ++f) {
+            double acc = taps[(size_t)(n_det - 1)];
+            for (int m = 1; m < n_det; ++m)
+                acc += 2.0 * taps[(size_t)(n_det - 1 + m)] * ct[(size_t)(((long)f * m) % N)];
+            hs[(size_t)f] = (float)(acc / (double)N);
+        }
+        e = cudaMalloc(&p->d_fft_tw, sizeof(float2) * (size_t)N);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_fft_h, sizeof(float) * (size_t)N);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_fft_tw, tw.data(), sizeof(float2) * (size_t)N, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_fft_h, hs.data(), sizeof(float) * (size_t)N, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -326,8 +367,12 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
         set_error("fbp_filter: ld_sino %d < n_det %d", ld_sino, p->D);
         return FBP_ERR_INVALID_ARG;
     }
-    cudaError_t e = launch_filter_direct_f32(*p, static_cast<const float *>(sino), ld_sino,
-                                             static_cast<float *>(filtered), stream);
+    cudaError_t e =
+        (p->filter_path == FBP_PATH_FFT)
+            ? launch_filter_fft_f32(*p, static_cast<const float *>(sino), ld_sino,
+                                    static_cast<float *>(filtered), stream)
+            : launch_filter_direct_f32(*p, static_cast<const float *>(sino), ld_sino,
+                                       static_cast<float *>(filtered), stream);
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_filter");
 }
 

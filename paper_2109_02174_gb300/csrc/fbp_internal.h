@@ -17,6 +17,7 @@ namespace fbp {
 constexpr int kBpTileX = 32;
 constexpr int kBpTileY = 32;
 constexpr int kBpChunk = 16;
+constexpr int kMaxFftLen = 8192;  // two N-point complex buffers in shared memory
 
 struct BpShape {
     int tile_x;
@@ -45,6 +46,8 @@ struct Plan {
     double2 *d_trig64;  // (cos th_i, sin th_i) / tau
     float *d_taps32;    // tau * h(m), m = -(D-1) .. D-1
     double *d_taps64;   // same in FP64
+    float2 *d_fft_tw;   // FFT route: exp(-2 pi i t / N), t < N
+    float *d_fft_h;     // FFT route: DFT_N of the circular taps, times 1/N (real, even)
     int *d_status;      // device status word (0 = ok)
 };
 
@@ -57,6 +60,10 @@ bool encode_q_map(const Plan &p, const void *q, int wraw, CUtensorMap *out);
 // Launchers (each returns the launch's cudaError_t).
 cudaError_t launch_filter_direct_f32(const Plan &p, const float *sino, int ld, float *q,
                                      cudaStream_t s);
+cudaError_t launch_filter_fft_f32(const Plan &p, const float *sino, int ld, float *q,
+                                  cudaStream_t s);
+size_t filter_fft_smem_bytes(int N);
+size_t filter_direct_smem_bytes(int D);
 cudaError_t launch_backproject_f32(const Plan &p, const CUtensorMap &qmap, float *image,
                                    cudaStream_t s);
 cudaError_t launch_radon_forward_f32(const Plan &p, const float *image, float *sino,

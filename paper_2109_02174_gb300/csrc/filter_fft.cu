@@ -1,0 +1,148 @@
+// Ramp filter Q = P * H (the convolution stated after Eq. 2), FFT route.
+//
+// With N >= 2*n_det - 1 the circular convolution of the zero-padded row with
+// the circularly arranged taps equals the linear convolution on [0, n_det),
+// so Q_i = IDFT_N( DFT_N(P_i) . H ) restricted to the first n_det bins, where
+// H = DFT_N of the taps tau*h(m) placed at m mod N.  H is real and even (the
+// taps are symmetric), so two real rows can share one complex transform:
+// z = P_i + i P_{i+1} gives IDFT(DFT(z) . H) = Q_i + i Q_{i+1} exactly.
+//
+// One CTA per row pair; the N-point complex transform is a radix-4 Stockham
+// autosort FFT (one radix-2 pass first when log2 N is odd) ping-ponging
+// between two shared-memory buffers; twiddles exp(-2 pi i t / N) come from a
+// plan table computed in FP64.  The 1/N of the inverse is folded into H.
+#include "fbp_internal.h"
+
+namespace fbp {
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 conj_if(float2 a, bool inv) { return inv ? make_float2(a.x, -a.y) : a; }
+
+// Radix-2 pass, sub-transform size ns -> 2 ns.
+__device__ void pass2(const float2 *x, float2 *y, const float2 *__restrict__ tw, int N, int ns,
+                      bool inv)
+{
+    const int half = N >> 1;
+    const int stride = N / (2 * ns);
+    for (int j = threadIdx.x; j < half; j += blockDim.x) {
+        const int k = j & (ns - 1);
+        const float2 w = conj_if(__ldg(&tw[k * stride]), inv);
+        const float2 a0 = x[j];
+        const float2 a1 = cmul(x[j + half], w);
+        const int o = ((j - k) << 1) + k;
+        y[o] = cadd(a0, a1);
+        y[o + ns] = csub(a0, a1);
+    }
+}
+
+// Radix-4 pass, sub-transform size ns -> 4 ns.
+__device__ void pass4(const float2 *x, float2 *y, const float2 *__restrict__ tw, int N, int ns,
+                      bool inv)
+{
+    const int q = N >> 2;
+    const int stride = N / (4 * ns);
+    for (int j = threadIdx.x; j < q; j += blockDim.x) {
+        const int k = j & (ns - 1);
+        const float2 w1 = conj_if(__ldg(&tw[k * stride]), inv);
+        const float2 w2 = conj_if(__ldg(&tw[2 * k * stride]), inv);
+        const float2 w3 = conj_if(__ldg(&tw[3 * k * stride]), inv);
+        const float2 a0 = x[j];
+        const float2 a1 = cmul(x[j + q], w1);
+        const float2 a2 = cmul(x[j + 2 * q], w2);
+        const float2 a3 = cmul(x[j + 3 * q], w3);
+        const float2 b0 = cadd(a0, a2);
+        const float2 b1 = csub(a0, a2);
+        const float2 b2 = cadd(a1, a3);
+        const float2 d = csub(a1, a3);
+        // forward: multiply by -i; inverse: by +i
+        const float2 b3 = inv ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+        const int o = ((j - k) << 2) + k;
+        y[o] = cadd(b0, b2);
+        y[o + ns] = cadd(b1, b3);
+        y[o + 2 * ns] = csub(b0, b2);
+        y[o + 3 * ns] = csub(b1, b3);
+    }
+}
+
+// Full transform; returns the buffer holding the result.
+__device__ float2 *fft(float2 *x, float2 *y, const float2 *__restrict__ tw, int N, int log2n,
+                       bool inv)
+{
+    int ns = 1;
+    if (log2n & 1) {
+        pass2(x, y, tw, N, ns, inv);
+        __syncthreads();
+        float2 *t = x; x = y; y = t;
+        ns = 2;
+    }
+    for (; ns < N; ns <<= 2) {
+        pass4(x, y, tw, N, ns, inv);
+        __syncthreads();
+        float2 *t = x; x = y; y = t;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(256)
+    filter_fft_f32_kernel(const float *__restrict__ sino, int ld, const float2 *__restrict__ tw,
+                          const float *__restrict__ hspec, float *__restrict__ q, int A, int D,
+                          int pitch, int N, int log2n)
+{
+    extern __shared__ float2 buf[];
+    float2 *x = buf;
+    float2 *y = buf + N;
+    const int i0 = 2 * blockIdx.x;
+    const bool two = i0 + 1 < A;
+    const float *p0 = sino + (size_t)i0 * ld;
+    const float *p1 = sino + (size_t)(two ? i0 + 1 : i0) * ld;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        float2 v = make_float2(0.0f, 0.0f);
+        if (j < D) {
+            v.x = p0[j];
+            v.y = two ? p1[j] : 0.0f;
+        }
+        x[j] = v;
+    }
+    __syncthreads();
+    float2 *z = fft(x, y, tw, N, log2n, false);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const float h = __ldg(&hspec[j]);
+        z[j] = make_float2(z[j].x * h, z[j].y * h);
+    }
+    __syncthreads();
+    float2 *other = (z == x) ? y : x;
+    z = fft(z, other, tw, N, log2n, true);
+    float *q0 = q + (size_t)i0 * pitch;
+    float *q1 = q + (size_t)(i0 + 1) * pitch;
+    for (int k = threadIdx.x; k < pitch; k += blockDim.x) {
+        const float2 v = (k < D) ? z[k] : make_float2(0.0f, 0.0f);
+        q0[k] = v.x;
+        if (two) q1[k] = v.y;
+    }
+}
+
+}  // namespace
+
+size_t filter_fft_smem_bytes(int N) { return sizeof(float2) * (size_t)(2 * N); }
+
+cudaError_t launch_filter_fft_f32(const Plan &p, const float *sino, int ld, float *q,
+                                  cudaStream_t s)
+{
+    const size_t smem = filter_fft_smem_bytes(p.fft_len);
+    cudaError_t e = cudaFuncSetAttribute(filter_fft_f32_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int log2n = 0;
+    while ((1 << log2n) < p.fft_len) ++log2n;
+    filter_fft_f32_kernel<<<(p.A + 1) / 2, 256, smem, s>>>(sino, ld, p.d_fft_tw, p.d_fft_h, q,
+                                                          p.A, p.D, p.pitch, p.fft_len, log2n);
+    return cudaGetLastError();
+}
+
+}  // namespace fbp

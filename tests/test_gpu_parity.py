@@ -52,11 +52,16 @@ def assert_parity(got, ref, max_rel=MAX_REL, rmse_rel=RMSE_REL):
 
 
 # ---------------------------------------------------------------- filter
+PATHS = {"direct": 3, "fft": 2}
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("kind", [0, 1, 2])
-def test_filter_matches_oracle(fbp, kind):
+def test_filter_matches_oracle(fbp, kind, path):
     A, D = 37, 211
     P = np.random.default_rng(20 + kind).standard_normal((A, D)).astype(np.float32)
-    plan = fbp.Plan(150, A, D, filter=kind)
+    plan = fbp.Plan(150, A, D, filter=kind, filter_path=PATHS[path])
+    assert plan.filter_path == PATHS[path]
     q = _np(plan.filter(_t(P)))
     assert q.shape == (A, plan.q_pitch) and plan.q_pitch % 8 == 0
     assert np.all(q[:, D:] == 0.0)
@@ -64,14 +69,28 @@ def test_filter_matches_oracle(fbp, kind):
     np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
 
 
-def test_filter_respects_row_stride(fbp):
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_filter_respects_row_stride(fbp, path):
     import torch
     A, D = 9, 50
     big = torch.randn(A, 64, device="cuda")
-    plan = fbp.Plan(30, A, D)
+    plan = fbp.Plan(30, A, D, filter_path=PATHS[path])
     q = _np(plan.filter(big[:, :D]))
     ref = oracle.filter_rows(big[:, :D].double().cpu().numpy(), 0, 1.0)
     np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("D,fft_len", [(2899, 0), (4096, 8192), (725, 4096), (1, 0), (2, 16)])
+def test_fft_filter_lengths(fbp, D, fft_len):
+    """FFT route at its size limits (N = 8192), an explicit longer N, and tiny rows."""
+    A = 5
+    P = np.random.default_rng(D).standard_normal((A, D)).astype(np.float32)
+    plan = fbp.Plan(8, A, D, filter_path=2, fft_len=fft_len)
+    assert plan.fft_len >= 2 * D - 1 and plan.fft_len & (plan.fft_len - 1) == 0
+    q = _np(plan.filter(_t(P)))
+    ref = oracle.filter_rows(P.astype(np.float64), 0, 1.0)
+    np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+    assert np.all(q[:, D:] == 0.0)
 
 
 # ---------------------------------------------------------------- backprojection
@@ -142,11 +161,11 @@ def test_deterministic_bits(fbp):
 
 
 # ---------------------------------------------------------------- whole FBP on the workloads
-def _check_slice(fbp, spec, nthreads=NTHREADS):
+def _check_slice(fbp, spec, nthreads=NTHREADS, **opts):
     th = synthetic.default_angles(spec.n_angles)
     sino32 = synthetic.sinogram(spec, th).astype(np.float32)
     plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
-                    det_spacing=spec.tau)
+                    det_spacing=spec.tau, **opts)
     got = _np(plan.reconstruct(_t(sino32)))
     plan.device_status()
     ref = oracle.fbp(sino32.astype(np.float64), th, spec.tau, spec.filter, spec.n_pix,
@@ -155,9 +174,10 @@ def _check_slice(fbp, spec, nthreads=NTHREADS):
     return errors(got, ref)
 
 
-def test_plain_slice_256(fbp):
-    """256x256, 180 angles, 363 bins, Ram-Lak, 10 ellipses (seed 1), noise-free."""
-    _check_slice(fbp, synthetic.cfg_plain())
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_plain_slice_256(fbp, path):
+    """256x256, 180 angles, 363 bins, Ram-Lak (FFT length 1024), 10 ellipses (seed 1)."""
+    _check_slice(fbp, synthetic.cfg_plain(), filter_path=PATHS[path], fft_len=1024)
 
 
 def test_float_slice_512_noisy(fbp):
