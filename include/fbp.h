@@ -155,6 +155,35 @@ fbp_status fbp_reconstruct(fbp_plan_t plan, const void *sino, int ld_sino, void 
  */
 fbp_status radon_forward(fbp_plan_t plan, const void *image, void *sino, fbp_stream_t stream);
 
+/* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
+#define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/*
+ * fbp_reconstruct for callers that cannot allocate device memory at the time
+ * they reconstruct (an acquisition loop with a fixed per-slice deadline cannot
+ * absorb the device-wide synchronisation of cudaMalloc/cudaFree; a host whose
+ * device memory belongs to another allocator or budget may not allocate at
+ * all).  The paper has no counterpart: it is a deployment convenience.
+ *
+ * Same result as fbp_reconstruct (same kernels, same bits); the filtered
+ * sinogram goes to a 256-byte-aligned static device array of
+ * FBP_STATIC_SCRATCH_BYTES compiled into the library instead of a caller
+ * workspace.  The call makes no cudaMalloc, cudaFree or other allocating call;
+ * the plan (whose tables fbp_plan allocated once, beforehand) is reused.
+ *   sino, ld_sino, image  as for fbp_reconstruct (device, caller-owned)
+ * Errors: FBP_ERR_BUDGET when the plan's workspace (fbp_workspace_bytes)
+ * exceeds FBP_STATIC_SCRATCH_BYTES; otherwise as fbp_reconstruct.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call on a device shares the one array and it keeps the last
+ * call's contents (nothing in it needs to start at zero: the filter writes
+ * every element the backprojection reads), so calls whose GPU work overlaps --
+ * on different streams, or from different threads -- race on it; order them on
+ * one stream or serialise them.
+ */
+fbp_status fbp_reconstruct_static(fbp_plan_t plan, const void *sino, int ld_sino, void *image,
+                                  fbp_stream_t stream);
+
 /* Read and clear the plan's device status word (synchronises the device):
  * FBP_OK, or FBP_ERR_TIMEOUT if a bounded device wait ran out since the last read. */
 fbp_status fbp_device_status(fbp_plan_t plan);

@@ -57,6 +57,7 @@ _SIGS = {
     "fbp_reconstruct": [_P, _P, _I, _P, _P, _P],
     "radon_forward": [_P, _P, _P, _P],
     "fbp_device_status": [_P],
+    "fbp_reconstruct_static": [_P, _P, _I, _P, _P],
 }
 
 
@@ -150,6 +151,11 @@ def fbp_reconstruct(plan: int, sino_ptr: int, ld_sino: int, image_ptr: int, work
 
 def radon_forward(plan: int, image_ptr: int, sino_ptr: int, stream: int):
     _check(load_library().radon_forward(plan, image_ptr, sino_ptr, stream))
+
+
+def fbp_reconstruct_static(plan: int, sino_ptr: int, ld_sino: int, image_ptr: int, stream: int):
+    """fbp_reconstruct with the library's static scratch array (no allocation)."""
+    _check(load_library().fbp_reconstruct_static(plan, sino_ptr, ld_sino, image_ptr, stream))
 
 
 def fbp_device_status(plan: int):
