@@ -71,7 +71,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -148,6 +148,30 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ our arm
+def _timed(fn, steps, stream, per_launch=False):
+    """Run fn() `steps` times between CUDA events on `stream`; returns total ms
+    (and the per-launch ms list when per_launch)."""
+    import torch
+    if per_launch:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        per = [a.elapsed_time(b) for a, b in evs]
+        return sum(per), per
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2109_02174_gb300 as fbp
@@ -168,73 +192,59 @@ def run_ours(args, rank, world, local_rank):
     sinos = [torch.from_numpy(h).to(dev) for h in host]
     works = [plan.empty_workspace() for _ in range(S)]
     images = [plan.empty_image() for _ in range(S)]
+    plans = [plan] * S
+    full = fbp.Batch(plans, sinos, images, works)
+    bp_only = fbp.Batch(plans, sinos, images, works, parts=fbp.FBP_BATCH_BACKPROJECT)
+    filt_only = fbp.Batch(plans, sinos, images, works, parts=fbp.FBP_BATCH_FILTER)
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
     ld = spec0.n_det
     resident_mb = S * (spec0.n_angles * spec0.n_det * 4 + plan.workspace_bytes +
                        spec0.n_pix ** 2 * 4) / 1e6
 
-    def step(ev=None):
-        for i in range(S):
-            fbp.fbp_filter(plan.handle, sinos[i].data_ptr(), ld, works[i].data_ptr(), sp)
-            if ev is not None:
-                ev[i][0].record(stream)
-            fbp.fbp_backproject(plan.handle, works[i].data_ptr(), images[i].data_ptr(), sp)
-            if ev is not None:
-                ev[i][1].record(stream)
-
     for _ in range(args.warmup):
-        step()
+        full.launch()
     torch.cuda.synchronize()
-    plan.device_status()
+    full.status()
 
-    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-           for _ in range(S)] for _ in range(args.steps)]
+    # ---- timed region: K steps of the batched hot path (filter + backprojection)
     clocks = ClockSampler(local_rank)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for k in range(args.steps):
-        step(ev[k])
-    t_end.record(stream)
-    torch.cuda.synchronize()
+    ms = _timed(full.launch, args.steps, stream)
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-    ms = t_start.elapsed_time(t_end)
-    bp_ms = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps) for i in range(S)]
-    plan.device_status()
-    if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
+    full.status()
 
-    # end to end through the C ABI with host buffers: pinned sinograms in, images out
+    # ---- the backprojection launch alone over the same buffers (roofline)
+    bp_only.launch()
+    _, bp_ms = _timed(bp_only.launch, max(args.steps // 4, 5), stream, per_launch=True)
+    filt_only.launch()
+    filt_ms = _timed(filt_only.launch, max(args.steps // 4, 5), stream) / max(args.steps // 4, 5)
+
+    # ---- the plain single-slice path (one fbp_reconstruct call per slice)
+    def plain_step():
+        for i in range(S):
+            fbp.fbp_reconstruct(plan.handle, sinos[i].data_ptr(), ld, images[i].data_ptr(),
+                                works[i].data_ptr(), sp)
+    plain_step()
+    plain_steps = max(args.steps // 10, 3)
+    plain_ms = _timed(plain_step, plain_steps, stream)
+
+    # ---- end to end through the C ABI from pinned host buffers
     h_sino = [torch.from_numpy(h).pin_memory() for h in host]
     h_img = [torch.empty((spec0.n_pix, spec0.n_pix), dtype=torch.float32).pin_memory()
              for _ in range(S)]
-
-    def e2e_step():
-        for i in range(S):
-            sinos[i].copy_(h_sino[i], non_blocking=True)
-            fbp.fbp_reconstruct(plan.handle, sinos[i].data_ptr(), ld, images[i].data_ptr(),
-                                works[i].data_ptr(), sp)
-            h_img[i].copy_(images[i], non_blocking=True)
-
-    e2e_step()
+    full.run_host(h_sino, h_img)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_steps = max(args.steps // 4, 5)
+    e2e_ms = _timed(lambda: full.run_host(h_sino, h_img), e2e_steps, stream)
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -251,28 +261,32 @@ def run_ours(args, rank, world, local_rank):
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_gups = FP32_LANES_PER_SM * sms * sm_mhz * 1e6 / OPS_PER_UPDATE / 1e9
     bp_mean = sum(bp_ms) / len(bp_ms)
-    achieved = upd / (bp_mean / 1e3) / 1e9
+    achieved = S * upd / (bp_mean / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "gupdates_per_s": value * upd / 1e9,
+        "plain_path": {"value": S * plain_steps / (plain_ms / 1e3), "unit": "slices/s",
+                       "what": "one fbp_reconstruct call per slice, same slices and stream"},
+        "filter_ms_per_step": filt_ms,
         "config": {"workload": WORKLOAD_NAME, "slices_per_step": S * world,
-                   "path": "plain single-slice calls (fbp_filter + fbp_backproject per slice)",
+                   "path": "batched: one captured graph per step (per-slice FFT filters + one "
+                           "persistent backprojection launch over all slices' tiles)",
                    "l2": f"inputs larger than L2: {resident_mb:.0f} MB resident per GPU",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "bp_f32_kernel", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "bp_persistent_kernel", "achieved": achieved,
                      "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
                      "traffic": None,
                      "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {sm_mhz:.0f} "
                                    f"MHz ({pk_kind} sm_max_mhz) / {OPS_PER_UPDATE} FP32 ops per "
                                    f"update",
-                     "launch_ms": bp_mean},
-        "e2e": {"value": total_slices / (e2e_ms / 1e3), "unit": "slices/s",
+                     "launch_ms": bp_mean, "updates_per_launch": S * upd},
+        "e2e": {"value": S * e2e_steps * world / (e2e_ms / 1e3), "unit": "slices/s",
                 "h2d_bytes_per_step": S * spec0.n_angles * spec0.n_det * 4,
                 "d2h_bytes_per_step": S * spec0.n_pix ** 2 * 4},
-        "gpu_launches": 2 * S * args.steps,
+        "gpu_launches": (S + 1) * args.steps,
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -283,6 +297,8 @@ def run_ours(args, rank, world, local_rank):
                                 "kind": "oracle",
                                 "sample": "one full slice of the workload (FP64 C oracle, "
                                           "filter + backprojection, all host cores)"}
+    for b in (full, bp_only, filt_only):
+        b.close()
     print(json.dumps(line), flush=True)
     return 0
 
@@ -290,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

@@ -120,10 +120,15 @@ fbp_status fbp_workspace_bytes(fbp_plan_t plan, size_t *bytes);
 fbp_status fbp_plan_query(fbp_plan_t plan, int *q_pitch, int *fft_len, int *filter_path);
 
 /*
- * Ramp filter, Q = P * H (the text after Eq. 2).
- *   sino      device [n_angles][ld_sino] of the plan's dtype, ld_sino >= n_det
- *   filtered  device [n_angles][q_pitch] of q_storage type; bins n_det .. q_pitch-1
- *             of every row are written as zero
+ * Ramp filter, Q = P * H (the text after Eq. 2), written in interpolation-ready
+ * form for fbp_backproject.
+ *   sino      device [n_angles][ld_sino] float, ld_sino >= n_det
+ *   filtered  device [n_angles][q_pitch] of the q_storage type (float, or half for
+ *             FBP_F16).  Row i holds, for every bin k = -1 .. n_det-1, the pair
+ *               mid_k = (Q_i[k] + Q_i[k+1]) / 2,   slope_k = Q_i[k+1] - Q_i[k]
+ *             at elements 2(k+1) and 2(k+1)+1, with Q_i zero outside [0, n_det)
+ *             (so the linear interpolant on [k, k+1] is mid_k + (u - k - 1/2) slope_k);
+ *             elements 2(n_det+1) .. q_pitch-1 are written as zero.
  */
 fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filtered,
                       fbp_stream_t stream);
@@ -132,8 +137,8 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
  * Backprojection, Eq. 2: image[r][c] = (pi/A) sum_i lerp(Q_i, u_i(r,c)) with
  * u_i = (x cos th_i + y sin th_i)/tau + (n_det-1)/2, angles summed in order
  * i = 0..A-1 (deterministic: same bits every run).
- *   filtered  device [n_angles][q_pitch] as written by fbp_filter
- *   image     device [n_pix][n_pix] of the plan's dtype, written once
+ *   filtered  device [n_angles][q_pitch] pairs as written by fbp_filter
+ *   image     device [n_pix][n_pix] float, written once
  */
 fbp_status fbp_backproject(fbp_plan_t plan, const void *filtered, void *image,
                            fbp_stream_t stream);
@@ -154,6 +159,64 @@ fbp_status fbp_reconstruct(fbp_plan_t plan, const void *sino, int ld_sino, void 
  *   sino   device [n_angles][n_det] float
  */
 fbp_status radon_forward(fbp_plan_t plan, const void *image, void *sino, fbp_stream_t stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many slices (any mix of sizes and plans) reconstructed by one captured CUDA
+ * graph: every slice's ramp filter, then one persistent backprojection launch
+ * per kernel configuration whose work list holds the pixel tiles of all its
+ * slices, most angles first.  Each slice goes through the same arithmetic as
+ * fbp_reconstruct with its plan, so its image is bit-identical to the one it
+ * gets alone.  (The paper reconstructs one image at a time; batching is this
+ * library's throughput form of the same Eq. 2.) */
+typedef struct fbp_batch_s *fbp_batch_t;
+
+typedef struct {
+    const void *sino;  /* device [n_angles][ld_sino] float of that slice */
+    int ld_sino;       /* >= n_det */
+    void *image;       /* device [n_pix][n_pix] float */
+    void *workspace;   /* device, >= fbp_workspace_bytes(plan), 16-byte aligned */
+} fbp_batch_io;
+
+/*
+ * Build a batch of n (1..64) slices: plans[i] with buffers io[i].  The buffer
+ * addresses are bound into the graph: refill the sinogram buffers and call
+ * fbp_batch_launch again to reconstruct new data.  The plans and buffers must
+ * outlive the batch.  Building allocates a small work list and records the
+ * graph (no kernel runs); `stream` is unused and may be NULL.
+ * Errors: FBP_ERR_INVALID_ARG, FBP_ERR_ALIGNMENT, FBP_ERR_UNSUPPORTED (FP64
+ * plans), FBP_ERR_OUT_OF_MEMORY, FBP_ERR_CUDA.
+ */
+fbp_status fbp_batch_build(fbp_batch_t *out, const fbp_plan_t *plans, int n,
+                           const fbp_batch_io *io, fbp_stream_t stream);
+
+/* Parts of a batch graph (fbp_batch_build records both). */
+enum { FBP_BATCH_FILTER = 1, FBP_BATCH_BACKPROJECT = 2 };
+
+/* fbp_batch_build recording only the given parts (a bitwise OR of FBP_BATCH_*),
+ * e.g. to time the backprojection launch alone over the same buffers. */
+fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int n,
+                                 const fbp_batch_io *io, int parts, fbp_stream_t stream);
+
+/* Enqueue the whole batch on `stream` (one graph launch). */
+fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream);
+
+/*
+ * The batch end to end from host memory, all on `stream`: each slice's
+ * sinogram (host, [n_angles][n_det] float, contiguous) is copied into the
+ * batch's device sinogram buffer, the graph runs, and each image is copied back
+ * to host_images[i] ([n_pix][n_pix] float).  One cudaMemcpy2DAsync /
+ * cudaMemcpyAsync per slice and direction; host buffers should be pinned for
+ * asynchronous copies.  Returns after enqueueing; synchronise the stream
+ * before reading the images.
+ */
+fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
+                              void *const *host_images, fbp_stream_t stream);
+
+/* Read and clear the batch's device status word (synchronises the device). */
+fbp_status fbp_batch_status(fbp_batch_t batch);
+
+/* Release the batch (synchronises the device).  NULL is a no-op. */
+fbp_status fbp_batch_destroy(fbp_batch_t batch);
 
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)

@@ -25,12 +25,18 @@ FBP_FILTER_RAM_LAK, FBP_FILTER_SHEPP_LOGAN, FBP_FILTER_NONE = 0, 1, 2
 FBP_F32, FBP_F64, FBP_F16 = 0, 1, 2
 FBP_ACC_PLAIN, FBP_ACC_KAHAN = 0, 1
 FBP_PATH_AUTO, FBP_PATH_TOEPLITZ_TC, FBP_PATH_FFT, FBP_PATH_DIRECT = 0, 1, 2, 3
+FBP_BATCH_FILTER, FBP_BATCH_BACKPROJECT = 1, 2
 
 
 class FbpError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class fbp_batch_io(ctypes.Structure):
+    _fields_ = [("sino", ctypes.c_void_p), ("ld_sino", ctypes.c_int),
+                ("image", ctypes.c_void_p), ("workspace", ctypes.c_void_p)]
 
 
 class fbp_options(ctypes.Structure):
@@ -58,6 +64,14 @@ _SIGS = {
     "radon_forward": [_P, _P, _P, _P],
     "fbp_device_status": [_P],
     "fbp_reconstruct_static": [_P, _P, _I, _P, _P],
+    "fbp_batch_build": [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io),
+                        _P],
+    "fbp_batch_build_parts": [ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
+                              ctypes.POINTER(fbp_batch_io), _I, _P],
+    "fbp_batch_launch": [_P, _P],
+    "fbp_batch_run_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+    "fbp_batch_status": [_P],
+    "fbp_batch_destroy": [_P],
 }
 
 
@@ -162,6 +176,34 @@ def fbp_device_status(plan: int):
     _check(load_library().fbp_device_status(plan))
 
 
+def fbp_batch_build(plans, ios, parts: int = FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT) -> int:
+    n = len(plans)
+    parr = (_P * n)(*plans)
+    iarr = (fbp_batch_io * n)(*ios)
+    h = _P()
+    _check(load_library().fbp_batch_build_parts(ctypes.byref(h), parr, n, iarr, int(parts), None))
+    return h.value
+
+
+def fbp_batch_run_host(batch: int, host_sino_ptrs, host_image_ptrs, stream: int):
+    n = len(host_sino_ptrs)
+    s = (_P * n)(*host_sino_ptrs)
+    i = (_P * n)(*host_image_ptrs)
+    _check(load_library().fbp_batch_run_host(batch, s, i, stream))
+
+
+def fbp_batch_launch(batch: int, stream: int):
+    _check(load_library().fbp_batch_launch(batch, stream))
+
+
+def fbp_batch_status(batch: int):
+    _check(load_library().fbp_batch_status(batch))
+
+
+def fbp_batch_destroy(batch: int):
+    _check(load_library().fbp_batch_destroy(batch))
+
+
 # ------------------------------------------------------------ tensor wrapper
 class Plan:
     """A reconstruction plan bound to torch tensors on the current CUDA device."""
@@ -242,3 +284,46 @@ class Plan:
 
     def device_status(self):
         fbp_device_status(self.handle)
+
+
+class Batch:
+    """A graph-captured batch over (plan, sinogram, image, workspace) tensors.
+
+    The tensors are bound at construction: refill the sinograms in place and
+    call ``launch()`` again for new data.  Keep plans and tensors alive.
+    """
+
+    def __init__(self, plans, sinos, images=None, workspaces=None,
+                 parts: int = FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT):
+        self.plans = list(plans)
+        self.sinos = list(sinos)
+        self.images = list(images) if images is not None else [p.empty_image() for p in self.plans]
+        self.workspaces = list(workspaces) if workspaces is not None else \
+            [p.empty_workspace() for p in self.plans]
+        ios = [fbp_batch_io(_ptr(s), s.stride(0), _ptr(i), _ptr(w))
+               for s, i, w in zip(self.sinos, self.images, self.workspaces)]
+        self.handle = fbp_batch_build([p.handle for p in self.plans], ios, parts)
+        self.updates = sum(p.n_pix * p.n_pix * p.n_angles for p in self.plans)
+
+    def launch(self, stream=None):
+        fbp_batch_launch(self.handle, _stream(stream))
+        return self.images
+
+    def run_host(self, host_sinos, host_images, stream=None):
+        """Host sinograms in, host images out (pinned CPU tensors), one stream."""
+        fbp_batch_run_host(self.handle, [_ptr(h) for h in host_sinos],
+                           [_ptr(h) for h in host_images], _stream(stream))
+
+    def status(self):
+        fbp_batch_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fbp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

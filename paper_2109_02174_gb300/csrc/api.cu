@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "backproject.cuh"
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -81,25 +82,86 @@ void set_error(const char *fmt, ...)
     g_err = buf;
 }
 
-bool encode_q_map(const Plan &p, const void *q, int wraw, CUtensorMap *out)
+bool encode_pairs_map(const Plan &p, const void *q, CUtensorMap *out)
 {
     EncodeTiledFn enc = encode_fn();
     if (enc == nullptr) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
         return false;
     }
-    const cuuint64_t dims[2] = {(cuuint64_t)p.D, (cuuint64_t)p.A};
-    const cuuint64_t strides[1] = {(cuuint64_t)p.pitch * 4u};
-    const cuuint32_t box[2] = {(cuuint32_t)wraw, 1u};
+    const int es = q_elem_bytes(p);
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * (p.D + 1)), (cuuint64_t)p.A};
+    const cuuint64_t strides[1] = {(cuuint64_t)p.pitch * (cuuint64_t)es};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * p.bp_wp), 1u};
     const cuuint32_t estr[2] = {1u, 1u};
-    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(q), dims, strides,
-                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const CUtensorMapDataType dt =
+        es == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = enc(out, dt, 2, const_cast<void *>(q), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
         return false;
     }
     return true;
+}
+
+BpSlice slice_desc(const Plan &p, float *image)
+{
+    BpSlice s;
+    std::memset(&s, 0, sizeof s);
+    s.trig64 = p.d_trig64;
+    s.image = image;
+    s.n = p.n;
+    s.A = p.A;
+    s.wp = p.bp_wp;
+    s.tiles_x = (p.n + 8 * p.bp_wx - 1) / (8 * p.bp_wx);
+    s.scale = p.scale32;
+    s.half_n = 0.5 * (double)(p.n - 1);
+    s.half_d = 0.5 * (double)(p.D - 1);
+    return s;
+}
+
+int tiles_of(const Plan &p)
+{
+    const int tx = 8 * p.bp_wx, ty = 32 * p.bp_wy;
+    return ((p.n + tx - 1) / tx) * ((p.n + ty - 1) / ty);
+}
+
+BpConfig bp_config(const Plan &p)
+{
+    BpConfig c;
+    c.wx = p.bp_wx;
+    c.wy = p.bp_wy;
+    c.half_pairs = p.q_storage == FBP_F16;
+    c.kahan = p.accumulate == FBP_ACC_KAHAN;
+    return c;
+}
+
+cudaError_t backproject_slice(const Plan &p, const void *q, float *image, cudaStream_t s)
+{
+    BpLaunch<1> L;
+    std::memset(&L, 0, sizeof L);
+    if (!encode_pairs_map(p, q, &L.maps[0])) return cudaErrorInvalidValue;
+    L.slices[0] = slice_desc(p, image);
+    L.items = nullptr;
+    L.n_items = tiles_of(p);
+    L.wp_max = p.bp_wp;
+    L.status = p.d_status;
+    return launch_backproject(L, bp_config(p), s);
+}
+
+// Detector window (pairs) a tile of tx x ty pixels needs per angle: the tile's
+// detector coordinates span ext = max_i (tx-1)|c_i| + (ty-1)|s_i| bins; the
+// window starts one bin below floor(umin), aligned down to `align` pairs, and
+// must hold the pair of round(u - base - 1/2) <= ext + align + 1.
+int window_pairs(const std::vector<double2> &trig, int tx, int ty, int align)
+{
+    double ext = 0.0;
+    for (const double2 &cs : trig)
+        ext = std::fmax(ext, (tx - 1) * std::fabs(cs.x) + (ty - 1) * std::fabs(cs.y));
+    const int wp = (int)std::ceil(ext + 1e-6) + align + 2;
+    return ((wp + align - 1) / align) * align;
 }
 
 }  // namespace fbp
@@ -186,8 +248,9 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         set_error("fbp_plan: dtype %d not built", o.dtype);
         return FBP_ERR_UNSUPPORTED;
     }
-    if (o.q_storage != FBP_F32 || o.accumulate != FBP_ACC_PLAIN) {
-        set_error("fbp_plan: q_storage/accumulate option not built");
+    if ((o.q_storage != FBP_F32 && o.q_storage != FBP_F16) ||
+        (o.accumulate != FBP_ACC_PLAIN && o.accumulate != FBP_ACC_KAHAN)) {
+        set_error("fbp_plan: q_storage %d / accumulate %d not built", o.q_storage, o.accumulate);
         return FBP_ERR_UNSUPPORTED;
     }
     if (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT &&
@@ -230,7 +293,7 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     p->n = n_pix;
     p->A = n_angles;
     p->D = n_det;
-    p->pitch = round_up(n_det, 8);
+    p->pitch = round_up(2 * (n_det + 1), 8);
     p->filter = (int)filter;
     p->dtype = o.dtype;
     p->q_storage = o.q_storage;
@@ -247,27 +310,29 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     }
 
     std::vector<double2> trig((size_t)n_angles);
-    double ext = 0.0;
-    const int tx = kBpTileX, ty = kBpTileY;
-    for (int i = 0; i < n_angles; ++i) {
-        const double c = std::cos(theta[(size_t)i]) / det_spacing;
-        const double s = std::sin(theta[(size_t)i]) / det_spacing;
-        trig[(size_t)i] = make_double2(c, s);
-        ext = std::fmax(ext, (tx - 1) * std::fabs(c) + (ty - 1) * std::fabs(s));
+    for (int i = 0; i < n_angles; ++i)
+        trig[(size_t)i] = make_double2(std::cos(theta[(size_t)i]) / det_spacing,
+                                       std::sin(theta[(size_t)i]) / det_spacing);
+    // Backprojection tile: the largest of 32x64, 32x32, 8x32 pixels whose
+    // detector window fits one TMA box (256 elements = 128 pairs), unless the
+    // options name one of them.
+    const int align = (o.q_storage == FBP_F16) ? 4 : 2;
+    const int shapes[3][2] = {{4, 2}, {4, 1}, {1, 1}};
+    int pick = -1;
+    for (int k = 0; k < 3 && pick < 0; ++k) {
+        const int tx = 8 * shapes[k][0], ty = 32 * shapes[k][1];
+        if ((o.tile_x || o.tile_y) && (o.tile_x != tx || o.tile_y != ty)) continue;
+        if (window_pairs(trig, tx, ty, align) <= 128) pick = k;
     }
-    // The window starts at base >= umin - 5 and must hold bins up to
-    // round(u - base - 1/2) + 1 <= ext + 6, for every pixel u of the tile.
-    const int wraw = round_up((int)std::ceil(ext + 1e-6) + 7, 4);
-    if (wraw > 256) {
+    if (pick < 0) {
         delete p;
-        set_error("fbp_plan: detector window of %d bins per tile exceeds 256 "
-                  "(det_spacing %.3g too small for the %dx%d tile)", wraw, det_spacing, tx, ty);
+        set_error("fbp_plan: no backprojection tile fits the detector window (det_spacing %.3g, "
+                  "tile %dx%d requested)", det_spacing, o.tile_x, o.tile_y);
         return FBP_ERR_UNSUPPORTED;
     }
-    p->bp.tile_x = tx;
-    p->bp.tile_y = ty;
-    p->bp.chunk = kBpChunk;
-    p->bp.wraw = wraw;
+    p->bp_wx = shapes[pick][0];
+    p->bp_wy = shapes[pick][1];
+    p->bp_wp = window_pairs(trig, 8 * p->bp_wx, 32 * p->bp_wy, align);
 
     std::vector<double> taps;
     make_taps((int)filter, n_det, det_spacing, taps);
@@ -340,7 +405,7 @@ fbp_status fbp_workspace_bytes(fbp_plan_t plan, size_t *bytes)
         set_error("fbp_workspace_bytes: NULL argument");
         return FBP_ERR_INVALID_ARG;
     }
-    *bytes = (size_t)p->A * (size_t)p->pitch * sizeof(float);
+    *bytes = (size_t)p->A * (size_t)p->pitch * (size_t)q_elem_bytes(*p);
     return FBP_OK;
 }
 
@@ -369,10 +434,9 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
     }
     cudaError_t e =
         (p->filter_path == FBP_PATH_FFT)
-            ? launch_filter_fft_f32(*p, static_cast<const float *>(sino), ld_sino,
-                                    static_cast<float *>(filtered), stream)
-            : launch_filter_direct_f32(*p, static_cast<const float *>(sino), ld_sino,
-                                       static_cast<float *>(filtered), stream);
+            ? launch_filter_fft(*p, static_cast<const float *>(sino), ld_sino, filtered, stream)
+            : launch_filter_direct(*p, static_cast<const float *>(sino), ld_sino, filtered,
+                                   stream);
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_filter");
 }
 
@@ -382,9 +446,8 @@ fbp_status fbp_backproject(fbp_plan_t plan, const void *filtered, void *image,
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     fbp_status st = check_call(p, "fbp_backproject", {filtered, image});
     if (st != FBP_OK) return st;
-    CUtensorMap map;
-    if (!encode_q_map(*p, filtered, p->bp.wraw, &map)) return FBP_ERR_CUDA;
-    cudaError_t e = launch_backproject_f32(*p, map, static_cast<float *>(image), stream);
+    cudaError_t e = backproject_slice(*p, filtered, static_cast<float *>(image), stream);
+    if (e == cudaErrorInvalidValue) return FBP_ERR_CUDA;  // tensor map encoding (message set)
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_backproject");
 }
 

@@ -1,27 +1,33 @@
 // FP32 backprojection (Eq. 2): pixel-driven, gather-only, deterministic.
 //
-// Work item = one tile of TX x TY pixels (one CTA).  Angles are processed in
-// chunks of CH.  For every angle the detector window the tile needs (wraw
-// bins starting at a 16-byte-aligned bin `base`) is brought into shared memory
-// by a 2D TMA load out of the filtered sinogram [A][pitch]; bins outside
-// [0, n_det) arrive as zeros (TMA out-of-bounds fill), which is exactly the
-// zero extension of the interpolation.  Two chunks are in flight (double
-// buffer, one mbarrier per stage).
+// Input: the filtered sinogram in interpolation-ready form, row i holding for
+// every bin k = -1 .. n_det-1 the pair
+//     (mid_k, slope_k) = ((Q[k] + Q[k+1]) / 2,  Q[k+1] - Q[k]),
+// Q being zero outside [0, n_det).  With k = floor(u) and w = u - k - 1/2,
+//     lerp(Q_i, u) = mid_k + w * slope_k                      (one FMA).
 //
-// Each staged window is rewritten once into (A'_k, B_k) pairs,
-//   B_k  = Q[base+k+1] - Q[base+k]
-//   A'_k = Q[base+k] - (k - 1/2) B_k
-// so that with the local coordinate v = u - base - 1/2 and k = round(v),
-//   lerp(Q, u) = Q[base+k] + (u - base - k) B_k = A'_k + v B_k,
-// one FMA per update.  k is taken from the bits of v + 1.5*2^23 (the sum is
-// rounded to an integer that lands in the low mantissa bits), so there is no
-// float-to-int conversion on the hot path.  v is a tile-local coordinate
-// (|v| < wraw), which keeps the FP32 position error near 1e-5 bins even where
-// the global detector coordinate is in the thousands.
+// Persistent, warp-specialised kernel.  The launch owns a list of work items,
+// each one TX x TY pixel tile of one slice (one launch may hold many slices of
+// different sizes); CTA b takes items b, b + grid, b + 2 grid, ...
+//   - warp NCW (the producer) walks the items' angle chunks: for each angle
+//     its lanes compute, in FP64, the first pair of the detector window the
+//     tile touches and the tile-local coordinate offset; lane 0 then issues
+//     one 2D TMA load per angle into a ring of NSTAGE shared-memory stages
+//     (pairs outside the detector arrive as zeros: TMA out-of-bounds fill,
+//     which is the zero extension of the interpolation);
+//   - warps 0..NCW-1 (consumers) wait for a stage's mbarrier, accumulate its
+//     angles into per-thread registers, and release the stage on a second
+//     mbarrier.  There is no block-wide barrier in the loop.
+// Per update a consumer computes the local coordinate v = u - base - 1/2 with
+// an FMA, rounds it with v + 1.5*2^23 (the integer lands in the low mantissa
+// bits and gives the shared-memory address directly), forms w = v - round(v),
+// loads the (mid, slope) pair and adds mid + w*slope.  Pixel pairs go through
+// the packed f32x2 FMA/ADD.  The local coordinate (|v| < window) keeps the FP32
+// position error near 1e-5 bins where the global detector coordinate is large.
 //
-// Every pixel sums its angles in order 0..A-1 in its own registers: no
-// atomics, no cross-CTA reduction, the same bits on every run.
-#include "fbp_internal.h"
+// Every pixel sums its angles in order 0..A-1 in registers: no atomics, no
+// cross-CTA reduction, the same bits on every run and in every batch.
+#include "backproject.cuh"
 #include "ptx.cuh"
 
 namespace fbp {
@@ -30,217 +36,298 @@ namespace {
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
 
-struct BpArgs {
-    const double2 *trig64;  // (cos, sin) / tau per angle
-    float *image;
-    int *status;
-    int n;
-    int A;
-    int wraw;
-    int nchunks;
-    float scale;    // pi / A
-    double half_n;  // (n - 1) / 2
-    double half_d;  // (n_det - 1) / 2
+__device__ __forceinline__ float2 lds_f2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ float2 lds_h2_as_f2(uint32_t addr)
+{
+    uint32_t h;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(h) : "r"(addr));
+    __half2 v = *reinterpret_cast<__half2 *>(&h);
+    return __half22float2(v);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <typename PairT>
+struct PairTraits;
+template <>
+struct PairTraits<float> {
+    static constexpr int kBytes = 8;   // one (mid, slope) pair
+    static constexpr int kAlign = 2;   // pairs per 16 bytes: window start granularity
+    static constexpr int kShift = 3;   // log2(kBytes)
+};
+template <>
+struct PairTraits<__half> {
+    static constexpr int kBytes = 4;
+    static constexpr int kAlign = 4;
+    static constexpr int kShift = 2;
 };
 
-// Shared-memory layout (byte offsets from a 128-byte aligned origin).
-struct BpSmem {
-    int raw_row;  // bytes per staged raw row (128-byte multiple: TMA destination alignment)
-    int tab_row;  // bytes per (A', B) row
-    int raw;      // [2][CH] raw rows
-    int tab;      // [CH] (A', B) rows
-    int prm;      // [2][CH] float4 (c, s, off, base bits) of the staged chunk
-    int cur;      // [CH] float4 of the chunk being computed
-    int bar;      // [2] mbarriers
-    int total;    // bytes including the alignment slack
-    __host__ __device__ static BpSmem make(int wraw, int ch)
+template <int NSTAGE, int CH>
+struct Layout {
+    int row;    // bytes per staged window row (128-byte multiple)
+    int stage;  // bytes per stage
+    int prm;    // offset of params [NSTAGE][CH] float4
+    int full;   // offset of full barriers [NSTAGE]
+    int empty;  // offset of empty barriers [NSTAGE]
+    int total;  // bytes including 128 of alignment slack
+    __host__ __device__ static Layout make(int wp_max, int pair_bytes)
     {
-        BpSmem s;
-        s.raw_row = ((wraw * 4 + 127) / 128) * 128;
-        s.tab_row = (wraw - 1) * 8;
-        s.raw = 0;
-        s.tab = s.raw + 2 * ch * s.raw_row;
-        s.prm = ((s.tab + ch * s.tab_row + 15) / 16) * 16;
-        s.cur = s.prm + 2 * ch * 16;
-        s.bar = s.cur + ch * 16;
-        s.total = s.bar + 16 + 128;
-        return s;
+        Layout L;
+        L.row = ((wp_max * pair_bytes + 127) / 128) * 128;
+        L.stage = CH * L.row;
+        L.prm = NSTAGE * L.stage;
+        L.full = L.prm + NSTAGE * CH * 16;
+        L.empty = L.full + NSTAGE * 8;
+        L.total = L.empty + NSTAGE * 8 + 128;
+        return L;
     }
 };
 
-template <int TX, int TY, int NT, int CH>
-struct BpCfg {
-    static constexpr int kWarps = NT / 32;
-    static constexpr int kWX = TX / 8;  // warp footprint is 8 x 4 pixels
-    static constexpr int kWY = kWarps / kWX;
-    static constexpr int kYStride = 4 * kWY;
-    static constexpr int kPPT = TY / kYStride;  // pixels per thread
-    static_assert(TX % 8 == 0 && kWX >= 1 && kWarps % kWX == 0, "tile width vs warps");
-    static_assert(TY % kYStride == 0 && kPPT >= 1, "tile height vs warps");
-    static_assert(CH <= 32, "one producer lane per angle of a chunk");
-};
-
-template <int TX, int TY, int NT, int CH>
-__global__ void __launch_bounds__(NT)
-    bp_f32_kernel(const __grid_constant__ CUtensorMap qmap, const BpArgs args)
+template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
+__global__ void __launch_bounds__(32 * (WX * WY + 1))
+    bp_persistent_kernel(const __grid_constant__ BpLaunch<MAXS> P)
 {
-    using C = BpCfg<TX, TY, NT, CH>;
+    constexpr int NCW = WX * WY;           // consumer warps
+    constexpr int TX = 8 * WX;             // tile width  (warp footprint 8 wide)
+    constexpr int TY = 32 * WY;            // tile height (warp covers 32 rows)
+    constexpr int PPT = 8;                 // pixels per consumer thread (rows ly0 + 4j)
+    constexpr int CH = kBpChunk;
+    constexpr int NSTAGE = kBpStages;
+    using TR = PairTraits<PairT>;
+    using L_t = Layout<NSTAGE, CH>;
+
     extern __shared__ __align__(128) unsigned char smem[];
-    const BpSmem L = BpSmem::make(args.wraw, CH);
-    const uint32_t pad = (128u - (smem_addr(smem) & 127u)) & 127u;
-    unsigned char *base_ptr = smem + pad;
+    const L_t L = L_t::make(P.wp_max, TR::kBytes);
+    const uint32_t base_addr = (smem_addr(smem) + 127u) & ~127u;
+    unsigned char *base_ptr = smem + (base_addr - smem_addr(smem));
     float4 *prm = reinterpret_cast<float4 *>(base_ptr + L.prm);
-    float4 *cur = reinterpret_cast<float4 *>(base_ptr + L.cur);
-    const uint32_t bar0 = smem_addr(base_ptr + L.bar);
-    const uint32_t raw0 = smem_addr(base_ptr + L.raw);
+    const uint32_t full0 = base_addr + (uint32_t)L.full;
+    const uint32_t empty0 = base_addr + (uint32_t)L.empty;
 
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    const int lane = tid & 31;
-    const int col0 = blockIdx.x * TX;
-    const int row0 = blockIdx.y * TY;
-    const double x0 = (double)col0 - args.half_n;
-    const double y0 = (double)row0 - args.half_n;
-    const int wraw = args.wraw;
-    const int wt = wraw - 1;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
 
-    if (tid == 0) {
-        prefetch_tensor_map(&qmap);
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(full0 + 8u * s, 1);
+            mbar_init(empty0 + 8u * s, NCW);
+        }
         fence_proxy_async_smem();
     }
     __syncthreads();
 
-    // Producer: warp 0 computes each angle's window base and local offset in
-    // FP64 (one lane per angle), then lane 0 issues the chunk's TMA loads.
-    auto produce = [&](int cc, int s) {
-        const int a0 = cc * CH;
-        const int na = min(CH, args.A - a0);
-        if (lane < na) {
-            const double2 cs = args.trig64[a0 + lane];
-            const double u0 = x0 * cs.x + y0 * cs.y + args.half_d;
-            const double umin = u0 + fmin(0.0, (double)(TX - 1) * cs.x) +
-                                fmin(0.0, (double)(TY - 1) * cs.y);
-            const int base = (__double2int_rd(umin) - 1) & ~3;
-            prm[s * CH + lane] = make_float4((float)cs.x, (float)cs.y,
-                                             (float)(u0 - (double)base - 0.5),
-                                             __int_as_float(base));
-        }
-        __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            const uint32_t bar = bar0 + 8u * s;
-            mbar_arrive_expect_tx(bar, (uint32_t)(na * wraw * 4));
-            for (int a = 0; a < na; ++a) {
-                const int base = __float_as_int(prm[s * CH + a].w);
-                tma_load_2d(raw0 + (uint32_t)((s * CH + a) * L.raw_row), &qmap, base, a0 + a,
-                            bar);
+    if (warp == NCW) {
+        // ------------------------------------------------------------ producer
+        uint32_t it = 0;
+        for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
+            const int2 wi = P.items ? P.items[item] : make_int2(0, item);
+            const BpSlice &S = P.slices[wi.x];
+            const CUtensorMap *map = &P.maps[wi.x];
+            const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
+            const double x0 = (double)(tx * TX) - S.half_n;
+            const double y0 = (double)(ty * TY) - S.half_n;
+            const int nch = (S.A + CH - 1) / CH;
+            for (int cc = 0; cc < nch; ++cc, ++it) {
+                const int s = (int)(it % NSTAGE);
+                const uint32_t use = it / NSTAGE;
+                bool ok = true;
+                if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * s, (use - 1) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                    return;
+                }
+                const int a0 = cc * CH;
+                const int na = min(CH, S.A - a0);
+                int pb = 0;
+                if (lane < na) {
+                    const double2 cs = S.trig64[a0 + lane];
+                    const double u0 = x0 * cs.x + y0 * cs.y + S.half_d;
+                    const double umin = u0 + fmin(0.0, (double)(TX - 1) * cs.x) +
+                                        fmin(0.0, (double)(TY - 1) * cs.y);
+                    // first pair of the window: pair p holds bin k = p - 1; start
+                    // one bin below floor(umin), aligned down to 16 bytes.
+                    pb = __double2int_rd(umin) & ~(TR::kAlign - 1);
+                    const int base = pb - 1;  // bin of the window's first pair
+                    prm[s * CH + lane] = make_float4((float)cs.x, (float)cs.y,
+                                                     (float)(u0 - (double)base - 0.5), 0.0f);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t bar = full0 + 8u * s;
+                    mbar_arrive_expect_tx(bar, (uint32_t)(na * S.wp * TR::kBytes));
+                }
+                __syncwarp();
+                // each lane issues its own angle's load (x in elements of PairT)
+                if (lane < na) {
+                    tma_load_2d(base_addr + (uint32_t)(s * L.stage + lane * L.row), map,
+                                2 * pb, a0 + lane, full0 + 8u * s);
+                }
             }
         }
-    };
-
-    if (warp == 0) {
-        produce(0, 0);
-        if (args.nchunks > 1) produce(1, 1);
+        return;
     }
 
-    // Per-thread pixels: column lx, rows ly0 + j * kYStride.
-    const int lx = (warp % C::kWX) * 8 + (lane & 7);
-    const int ly0 = (warp / C::kWX) * 4 + (lane >> 3);
+    // ---------------------------------------------------------------- consumers
+    const int lx = (warp % WX) * 8 + (lane & 7);
+    const int ly0 = (warp / WX) * 32 + (lane >> 3);
     const float lxf = (float)lx;
-    float lyf[C::kPPT];
-    float acc[C::kPPT];
+    float2 ypair[PPT / 2];
 #pragma unroll
-    for (int j = 0; j < C::kPPT; ++j) {
-        lyf[j] = (float)(ly0 + j * C::kYStride);
-        acc[j] = 0.0f;
-    }
+    for (int jj = 0; jj < PPT / 2; ++jj)
+        ypair[jj] = make_float2((float)(ly0 + 8 * jj), (float)(ly0 + 8 * jj + 4));
+    const float2 kM2 = make_float2(kMagic, kMagic);
+    const float2 kNegM2 = make_float2(-kMagic, -kMagic);
+    const float2 kNeg1 = make_float2(-1.0f, -1.0f);
 
-    for (int cc = 0; cc < args.nchunks; ++cc) {
-        const int s = cc & 1;
-        const uint32_t parity = (uint32_t)((cc >> 1) & 1);
-        const int na = min(CH, args.A - cc * CH);
-        const bool ok = mbar_wait_bounded(bar0 + 8u * s, parity);
-        if (ok) {
-            const unsigned char *raw_s = base_ptr + L.raw + s * CH * L.raw_row;
-            for (int idx = tid; idx < na * wt; idx += NT) {
-                const int a = idx / wt;
-                const int k = idx - a * wt;
-                const float *r = reinterpret_cast<const float *>(raw_s + a * L.raw_row);
-                const float q0 = r[k];
-                const float b = r[k + 1] - q0;
-                reinterpret_cast<float2 *>(base_ptr + L.tab + a * L.tab_row)[k] =
-                    make_float2(fmaf(0.5f - (float)k, b, q0), b);
-            }
-            if (tid < na) cur[tid] = prm[s * CH + tid];
-        }
-        if (__syncthreads_or(!ok)) {
-            // A TMA load did not land within the limit: record it, give the
-            // copies in flight a bounded chance to finish, and leave.
-            if (tid == 0) {
-                *reinterpret_cast<volatile int *>(args.status) = FBP_ERR_TIMEOUT;
-                mbar_wait_bounded(bar0 + 8u * s, parity);
-                if (cc + 1 < args.nchunks)
-                    mbar_wait_bounded(bar0 + 8u * (s ^ 1), (uint32_t)(((cc + 1) >> 1) & 1));
-            }
-            __syncthreads();
-            return;
-        }
-        if (warp == 0 && cc + 2 < args.nchunks) produce(cc + 2, s);
+    uint32_t it = 0;
+    for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
+        const int2 wi = P.items ? P.items[item] : make_int2(0, item);
+        const BpSlice &S = P.slices[wi.x];
+        const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
+        const int nch = (S.A + CH - 1) / CH;
+        float acc[PPT];
+        float cmp[KAHAN ? PPT : 1];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) acc[j] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < (KAHAN ? PPT : 1); ++j) cmp[j] = 0.0f;
 
-        const uint32_t tab_off = pad + (uint32_t)L.tab - (kMagicBits << 3);
+        for (int cc = 0; cc < nch; ++cc, ++it) {
+            const int s = (int)(it % NSTAGE);
+            const uint32_t parity = (it / NSTAGE) & 1u;
+            const bool ok = mbar_wait_bounded(full0 + 8u * s, parity);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                return;
+            }
+            const int na = min(CH, S.A - cc * CH);
+            const uint32_t stage_addr = base_addr + (uint32_t)(s * L.stage);
+            const float4 *pp = prm + s * CH;
 #pragma unroll 2
-        for (int a = 0; a < na; ++a) {
-            const float4 p = cur[a];
-            const uint32_t cb = tab_off + (uint32_t)(a * L.tab_row);
-            const float xc = fmaf(lxf, p.x, p.z);
+            for (int a = 0; a < na; ++a) {
+                const float4 p = pp[a];
+                const uint32_t cb =
+                    stage_addr + (uint32_t)(a * L.row) - (kMagicBits << TR::kShift);
+                const float xc = fmaf(lxf, p.x, p.z);
+                const float2 xc2 = make_float2(xc, xc);
+                const float2 s2 = make_float2(p.y, p.y);
 #pragma unroll
-            for (int j = 0; j < C::kPPT; ++j) {
-                const float v = fmaf(lyf[j], p.y, xc);
-                const float t = __fadd_rn(v, kMagic);
-                const uint32_t o = (__float_as_uint(t) << 3) + cb;
-                const float2 ab = *reinterpret_cast<const float2 *>(smem + o);
-                acc[j] += fmaf(v, ab.y, ab.x);
+                for (int jj = 0; jj < PPT / 2; ++jj) {
+                    const float2 v = __ffma2_rn(ypair[jj], s2, xc2);
+                    const float2 t = __fadd2_rn(v, kM2);
+                    const float2 kf = __fadd2_rn(t, kNegM2);
+                    const float2 w = __ffma2_rn(kf, kNeg1, v);
+                    const uint32_t o0 = (__float_as_uint(t.x) << TR::kShift) + cb;
+                    const uint32_t o1 = (__float_as_uint(t.y) << TR::kShift) + cb;
+                    float2 q0, q1;
+                    if constexpr (TR::kBytes == 8) {
+                        q0 = lds_f2(o0);
+                        q1 = lds_f2(o1);
+                    } else {
+                        q0 = lds_h2_as_f2(o0);
+                        q1 = lds_h2_as_f2(o1);
+                    }
+                    const float v0 = fmaf(w.x, q0.y, q0.x);
+                    const float v1 = fmaf(w.y, q1.y, q1.x);
+                    if constexpr (KAHAN) {
+                        const float y0 = v0 - cmp[2 * jj];
+                        const float t0 = acc[2 * jj] + y0;
+                        cmp[2 * jj] = (t0 - acc[2 * jj]) - y0;
+                        acc[2 * jj] = t0;
+                        const float y1 = v1 - cmp[2 * jj + 1];
+                        const float t1 = acc[2 * jj + 1] + y1;
+                        cmp[2 * jj + 1] = (t1 - acc[2 * jj + 1]) - y1;
+                        acc[2 * jj + 1] = t1;
+                    } else {
+                        acc[2 * jj] += v0;
+                        acc[2 * jj + 1] += v1;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8u * s);
+        }
+
+        const int col = tx * TX + lx;
+        if (col < S.n) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int row = ty * TY + ly0 + 4 * j;
+                if (row < S.n) S.image[(size_t)row * S.n + col] = acc[j] * S.scale;
             }
         }
-        __syncthreads();
-    }
-
-    const int col = col0 + lx;
-#pragma unroll
-    for (int j = 0; j < C::kPPT; ++j) {
-        const int row = row0 + ly0 + j * C::kYStride;
-        if (row < args.n && col < args.n)
-            args.image[(size_t)row * args.n + col] = acc[j] * args.scale;
     }
 }
 
-constexpr int kTX = kBpTileX, kTY = kBpTileY, kNT = 256, kCH = kBpChunk;
+template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
+cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
+{
+    using L_t = Layout<kBpStages, kBpChunk>;
+    const L_t L = L_t::make(P.wp_max, PairTraits<PairT>::kBytes);
+    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, MAXS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L.total);
+    if (e != cudaSuccess) return e;
+    const int threads = 32 * (WX * WY + 1);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, L.total);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
+    if (grid > P.n_items) grid = P.n_items;
+    if (grid < 1) grid = 1;
+    kern<<<grid, threads, L.total, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int MAXS>
+cudaError_t dispatch(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit, cudaStream_t s)
+{
+    const bool h = c.half_pairs, k = c.kahan;
+    if (c.wx == 4 && c.wy == 2) {
+        if (!h && !k) return launch_one<float, false, 4, 2, MAXS>(P, grid_limit, s);
+        if (!h && k) return launch_one<float, true, 4, 2, MAXS>(P, grid_limit, s);
+        if (h && !k) return launch_one<__half, false, 4, 2, MAXS>(P, grid_limit, s);
+        return launch_one<__half, true, 4, 2, MAXS>(P, grid_limit, s);
+    }
+    if (c.wx == 4 && c.wy == 1) {
+        if (!h && !k) return launch_one<float, false, 4, 1, MAXS>(P, grid_limit, s);
+        if (!h && k) return launch_one<float, true, 4, 1, MAXS>(P, grid_limit, s);
+        if (h && !k) return launch_one<__half, false, 4, 1, MAXS>(P, grid_limit, s);
+        return launch_one<__half, true, 4, 1, MAXS>(P, grid_limit, s);
+    }
+    if (c.wx == 1 && c.wy == 1) {
+        if (!h && !k) return launch_one<float, false, 1, 1, MAXS>(P, grid_limit, s);
+        if (!h && k) return launch_one<float, true, 1, 1, MAXS>(P, grid_limit, s);
+        if (h && !k) return launch_one<__half, false, 1, 1, MAXS>(P, grid_limit, s);
+        return launch_one<__half, true, 1, 1, MAXS>(P, grid_limit, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 }  // namespace
 
-cudaError_t launch_backproject_f32(const Plan &p, const CUtensorMap &qmap, float *image,
-                                   cudaStream_t s)
+cudaError_t launch_backproject(const BpLaunch<1> &P, const BpConfig &c, cudaStream_t s)
 {
-    BpArgs a;
-    a.trig64 = p.d_trig64;
-    a.image = image;
-    a.status = p.d_status;
-    a.n = p.n;
-    a.A = p.A;
-    a.wraw = p.bp.wraw;
-    a.nchunks = (p.A + kCH - 1) / kCH;
-    a.scale = p.scale32;
-    a.half_n = 0.5 * (double)(p.n - 1);
-    a.half_d = 0.5 * (double)(p.D - 1);
-    const BpSmem L = BpSmem::make(a.wraw, kCH);
-    auto kern = bp_f32_kernel<kTX, kTY, kNT, kCH>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e != cudaSuccess) return e;
-    dim3 grid((p.n + kTX - 1) / kTX, (p.n + kTY - 1) / kTY);
-    kern<<<grid, kNT, L.total, s>>>(qmap, a);
-    return cudaGetLastError();
+    return dispatch<1>(P, c, 0, s);
+}
+
+cudaError_t launch_backproject_batch(const BpLaunch<kBpMaxSlices> &P, const BpConfig &c,
+                                     int grid_limit, cudaStream_t s)
+{
+    return dispatch<kBpMaxSlices>(P, c, grid_limit, s);
 }
 
 }  // namespace fbp

@@ -1,0 +1,52 @@
+// Launch description of the persistent backprojection kernel (backproject.cu).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "fbp_internal.h"
+
+namespace fbp {
+
+constexpr int kBpStages = 4;      // shared-memory ring depth (chunks of kBpChunk angles)
+constexpr int kBpMaxSlices = 64;  // slices per batched launch (tensor maps in the parameters)
+
+// One slice of a launch.
+struct BpSlice {
+    const double2 *trig64;  // (cos, sin) / tau per angle
+    float *image;           // [n][n]
+    int n;
+    int A;
+    int wp;       // detector window per tile and angle, in (mid, slope) pairs
+    int tiles_x;  // tiles per image row
+    float scale;  // pi / A
+    int pad_;
+    double half_n;  // (n - 1) / 2
+    double half_d;  // (n_det - 1) / 2
+};
+
+// Kernel parameters: one tensor map per slice (over that slice's filtered
+// pairs [A][pitch]) and the work list.  items == nullptr means a single slice
+// whose items are its tiles 0 .. n_items-1 in order.
+template <int MAXS>
+struct BpLaunch {
+    CUtensorMap maps[MAXS];
+    BpSlice slices[MAXS];
+    const int2 *items;  // (slice, tile) in schedule order
+    int n_items;
+    int wp_max;  // largest wp over the slices (sizes the shared-memory rows)
+    int *status;
+};
+
+// Template choice: tile = (8 wx) x (32 wy) pixels, wx*wy consumer warps.
+struct BpConfig {
+    int wx;
+    int wy;
+    bool half_pairs;  // FP16-stored (mid, slope) pairs
+    bool kahan;       // Kahan-compensated sum over angles
+};
+
+cudaError_t launch_backproject(const BpLaunch<1> &P, const BpConfig &c, cudaStream_t s);
+cudaError_t launch_backproject_batch(const BpLaunch<kBpMaxSlices> &P, const BpConfig &c,
+                                     int grid_limit, cudaStream_t s);
+
+}  // namespace fbp

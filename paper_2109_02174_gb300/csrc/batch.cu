@@ -1,0 +1,313 @@
+// Batched reconstruction of many slices (possibly of different sizes) as one
+// CUDA graph: each slice's ramp filter, then ONE persistent backprojection
+// launch per kernel configuration whose work list holds the tiles of all
+// slices, costliest first.  Every slice goes through the same arithmetic as
+// fbp_reconstruct with its plan (same tile shape, same window, same angle
+// order), so its image is bit-identical to the one it gets alone.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "backproject.cuh"
+#include "fbp_internal.h"
+
+namespace fbp {
+BpSlice slice_desc(const Plan &p, float *image);
+int tiles_of(const Plan &p);
+BpConfig bp_config(const Plan &p);
+}  // namespace fbp
+
+using namespace fbp;
+
+struct fbp_batch_s {
+    int device;
+    int n;
+    std::vector<const Plan *> plans;
+    std::vector<fbp_batch_io> io;
+    std::vector<int2 *> d_items;  // one work list per kernel configuration
+    int *d_status;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    long long updates;
+    int parts;
+};
+
+namespace {
+
+void free_batch(fbp_batch_s *b)
+{
+    if (b == nullptr) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int2 *p : b->d_items) cudaFree(p);
+    cudaFree(b->d_status);
+    delete b;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Enqueue the batch on stream s (used once, under stream capture).
+cudaError_t enqueue(fbp_batch_s *b, cudaStream_t s,
+                    const std::vector<std::vector<int>> &groups,
+                    const std::vector<std::vector<int2>> &items)
+{
+    for (int i = 0; i < b->n && (b->parts & FBP_BATCH_FILTER); ++i) {
+        const Plan &p = *b->plans[(size_t)i];
+        const fbp_batch_io &io = b->io[(size_t)i];
+        cudaError_t e = (p.filter_path == FBP_PATH_FFT)
+                            ? launch_filter_fft(p, static_cast<const float *>(io.sino),
+                                                io.ld_sino, io.workspace, s)
+                            : launch_filter_direct(p, static_cast<const float *>(io.sino),
+                                                   io.ld_sino, io.workspace, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (size_t g = 0; g < groups.size() && (b->parts & FBP_BATCH_BACKPROJECT); ++g) {
+        BpLaunch<kBpMaxSlices> L;
+        std::memset(&L, 0, sizeof L);
+        const std::vector<int> &members = groups[g];
+        for (size_t m = 0; m < members.size(); ++m) {
+            const int i = members[m];
+            const Plan &p = *b->plans[(size_t)i];
+            if (!encode_pairs_map(p, b->io[(size_t)i].workspace, &L.maps[m]))
+                return cudaErrorInvalidValue;
+            L.slices[m] = slice_desc(p, static_cast<float *>(b->io[(size_t)i].image));
+            L.wp_max = std::max(L.wp_max, p.bp_wp);
+        }
+        L.items = b->d_items[g];
+        L.n_items = (int)items[g].size();
+        L.status = b->d_status;
+        cudaError_t e = launch_backproject_batch(L, bp_config(*b->plans[(size_t)members[0]]), 0, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+fbp_status fbp_batch_build(fbp_batch_t *out, const fbp_plan_t *plans, int n,
+                           const fbp_batch_io *io, fbp_stream_t stream)
+{
+    return fbp_batch_build_parts(out, plans, n, io, FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT,
+                                 stream);
+}
+
+fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int n,
+                                 const fbp_batch_io *io, int parts, fbp_stream_t stream)
+{
+    if (out == nullptr) {
+        set_error("fbp_batch_build: out is NULL");
+        return FBP_ERR_INVALID_ARG;
+    }
+    if (parts <= 0 || (parts & ~(FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT)) != 0) {
+        set_error("fbp_batch_build: parts %d is not a combination of FBP_BATCH_* flags", parts);
+        return FBP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (plans == nullptr || io == nullptr || n < 1 || n > kBpMaxSlices) {
+        set_error("fbp_batch_build: need 1..%d slices with plans and buffers (got %d)",
+                  kBpMaxSlices, n);
+        return FBP_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_error("fbp_batch_build: no current CUDA device");
+        return FBP_ERR_CUDA;
+    }
+    for (int i = 0; i < n; ++i) {
+        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+        const fbp_batch_io &b = io[i];
+        if (p == nullptr || p->device != dev) {
+            set_error("fbp_batch_build: slice %d: NULL plan or plan of another device", i);
+            return FBP_ERR_INVALID_ARG;
+        }
+        if (p->dtype != FBP_F32) {
+            set_error("fbp_batch_build: slice %d: only FP32 plans batch", i);
+            return FBP_ERR_UNSUPPORTED;
+        }
+        if (!b.sino || !b.image || !b.workspace || b.ld_sino < p->D) {
+            set_error("fbp_batch_build: slice %d: NULL buffer or ld_sino < n_det", i);
+            return FBP_ERR_INVALID_ARG;
+        }
+        if (!aligned16(b.sino) || !aligned16(b.image) || !aligned16(b.workspace)) {
+            set_error("fbp_batch_build: slice %d: buffer not 16-byte aligned", i);
+            return FBP_ERR_ALIGNMENT;
+        }
+    }
+
+    fbp_batch_s *b = new fbp_batch_s();
+    b->device = dev;
+    b->n = n;
+    b->d_status = nullptr;
+    b->graph = nullptr;
+    b->exec = nullptr;
+    b->updates = 0;
+    b->parts = parts;
+    for (int i = 0; i < n; ++i) {
+        b->plans.push_back(reinterpret_cast<const Plan *>(plans[i]));
+        b->io.push_back(io[i]);
+        b->updates += (long long)b->plans.back()->n * b->plans.back()->n * b->plans.back()->A;
+    }
+
+    // Group slices by kernel configuration; one work list per group, tiles of
+    // the slices with the most angles first (every tile of a slice costs the same).
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_cfg;
+    for (int i = 0; i < n; ++i) {
+        const BpConfig c = bp_config(*b->plans[(size_t)i]);
+        by_cfg[std::make_tuple(c.wx, c.wy, (int)c.half_pairs, (int)c.kahan)].push_back(i);
+    }
+    std::vector<std::vector<int>> groups;
+    std::vector<std::vector<int2>> items;
+    for (auto &kv : by_cfg) {
+        std::vector<int> members = kv.second;
+        std::stable_sort(members.begin(), members.end(), [&](int a, int c) {
+            const Plan &pa = *b->plans[(size_t)a], &pc = *b->plans[(size_t)c];
+            return pa.A > pc.A;
+        });
+        std::vector<int2> list;
+        // interleave slices of equal angle count tile by tile
+        size_t i0 = 0;
+        while (i0 < members.size()) {
+            size_t i1 = i0;
+            while (i1 < members.size() &&
+                   b->plans[(size_t)members[i1]]->A == b->plans[(size_t)members[i0]]->A)
+                ++i1;
+            int max_tiles = 0;
+            for (size_t m = i0; m < i1; ++m)
+                max_tiles = std::max(max_tiles, tiles_of(*b->plans[(size_t)members[m]]));
+            for (int t = 0; t < max_tiles; ++t)
+                for (size_t m = i0; m < i1; ++m)
+                    if (t < tiles_of(*b->plans[(size_t)members[m]]))
+                        list.push_back(make_int2((int)m, t));
+            i0 = i1;
+        }
+        groups.push_back(members);
+        items.push_back(list);
+    }
+
+    cudaError_t e = cudaMalloc(&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+    for (size_t g = 0; g < items.size() && e == cudaSuccess; ++g) {
+        int2 *d = nullptr;
+        e = cudaMalloc(&d, sizeof(int2) * items[g].size());
+        if (e == cudaSuccess) {
+            b->d_items.push_back(d);
+            e = cudaMemcpy(d, items[g].data(), sizeof(int2) * items[g].size(),
+                           cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) {
+        free_batch(b);
+        set_error("fbp_batch_build: %s", cudaGetErrorString(e));
+        return FBP_ERR_OUT_OF_MEMORY;
+    }
+
+    // Capture the whole batch once into a graph on a private stream.
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = enqueue(b, cs, groups, items);
+        cudaError_t ee = cudaStreamEndCapture(cs, &b->graph);
+        e = (le != cudaSuccess) ? le : ee;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        set_error("fbp_batch_build: graph capture: %s", cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
+    }
+    (void)stream;
+    *out = reinterpret_cast<fbp_batch_t>(b);
+    return FBP_OK;
+}
+
+fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream)
+{
+    fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
+    if (b == nullptr) {
+        set_error("fbp_batch_launch: batch is NULL");
+        return FBP_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, stream);
+    if (e != cudaSuccess) {
+        set_error("fbp_batch_launch: %s", cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
+                              void *const *host_images, fbp_stream_t stream)
+{
+    fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
+    if (b == nullptr || host_sinos == nullptr || host_images == nullptr) {
+        set_error("fbp_batch_run_host: NULL argument");
+        return FBP_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < b->n; ++i) {
+        const Plan &p = *b->plans[(size_t)i];
+        const fbp_batch_io &io = b->io[(size_t)i];
+        if (host_sinos[i] == nullptr || host_images[i] == nullptr) {
+            set_error("fbp_batch_run_host: slice %d: NULL host buffer", i);
+            return FBP_ERR_INVALID_ARG;
+        }
+        cudaError_t e = cudaMemcpy2DAsync(const_cast<void *>(io.sino), sizeof(float) * io.ld_sino,
+                                          host_sinos[i], sizeof(float) * p.D, sizeof(float) * p.D,
+                                          p.A, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) {
+            set_error("fbp_batch_run_host: sinogram copy: %s", cudaGetErrorString(e));
+            return FBP_ERR_CUDA;
+        }
+    }
+    fbp_status st = fbp_batch_launch(batch, stream);
+    if (st != FBP_OK) return st;
+    for (int i = 0; i < b->n; ++i) {
+        const Plan &p = *b->plans[(size_t)i];
+        cudaError_t e = cudaMemcpyAsync(host_images[i], b->io[(size_t)i].image,
+                                        sizeof(float) * (size_t)p.n * (size_t)p.n,
+                                        cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) {
+            set_error("fbp_batch_run_host: image copy: %s", cudaGetErrorString(e));
+            return FBP_ERR_CUDA;
+        }
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_batch_status(fbp_batch_t batch)
+{
+    fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
+    if (b == nullptr) {
+        set_error("fbp_batch_status: batch is NULL");
+        return FBP_ERR_INVALID_ARG;
+    }
+    int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, b->d_status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        set_error("fbp_batch_status: %s", cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
+    }
+    if (v != 0) {
+        set_error("device status %d: a bounded device wait ran out", v);
+        return (fbp_status)v;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_batch_destroy(fbp_batch_t batch)
+{
+    fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
+    if (b == nullptr) return FBP_OK;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return FBP_OK;
+}
+
+}  // extern "C"

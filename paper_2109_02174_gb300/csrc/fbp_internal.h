@@ -11,26 +11,14 @@
 
 namespace fbp {
 
-// Launch shape of the FP32 backprojection.  A work item is one tile of
-// tile_x x tile_y pixels; its detector window per angle is `wraw` bins long
-// (a multiple of 4, at most 256 = the TMA box limit).
-constexpr int kBpTileX = 32;
-constexpr int kBpTileY = 32;
-constexpr int kBpChunk = 16;
-constexpr int kMaxFftLen = 8192;  // two N-point complex buffers in shared memory
-
-struct BpShape {
-    int tile_x;
-    int tile_y;
-    int chunk;  // angles staged per shared-memory window
-    int wraw;
-};
+constexpr int kBpChunk = 16;      // angles per shared-memory stage of the backprojection
+constexpr int kMaxFftLen = 8192;  // FP32 FFT route: two N-point complex buffers in shared memory
 
 struct Plan {
     int n;      // image side
     int A;      // angles
     int D;      // detector bins
-    int pitch;  // row pitch (elements) of the filtered sinogram
+    int pitch;  // row pitch of the filtered sinogram, in elements of q_storage
     int filter;
     int dtype;
     int q_storage;
@@ -39,7 +27,11 @@ struct Plan {
     int fft_len;
     double tau;
     int device;
-    BpShape bp;
+    // Backprojection launch shape: tile (8 bp_wx) x (32 bp_wy) pixels and the
+    // detector window per tile and angle, in (mid, slope) pairs.
+    int bp_wx;
+    int bp_wy;
+    int bp_wp;
     float scale32;   // pi / A
     double scale64;  // pi / A
     // Device tables owned by the plan.
@@ -51,21 +43,26 @@ struct Plan {
     int *d_status;      // device status word (0 = ok)
 };
 
+// Element size of the filtered sinogram.
+inline int q_elem_bytes(const Plan &p) { return p.q_storage == FBP_F16 ? 2 : 4; }
+
 // Thread-local error message for fbp_last_error().
 void set_error(const char *fmt, ...);
 
-// Tensor map of a filtered sinogram [A][pitch] (4-byte elements), box {wraw, 1}.
-bool encode_q_map(const Plan &p, const void *q, int wraw, CUtensorMap *out);
+// Tensor map over the filtered pairs of one slice: [A][2 (D+1)] elements of the
+// q_storage type with row stride pitch, box {2 wp, 1}.
+bool encode_pairs_map(const Plan &p, const void *q, CUtensorMap *out);
 
-// Launchers (each returns the launch's cudaError_t).
-cudaError_t launch_filter_direct_f32(const Plan &p, const float *sino, int ld, float *q,
-                                     cudaStream_t s);
-cudaError_t launch_filter_fft_f32(const Plan &p, const float *sino, int ld, float *q,
-                                  cudaStream_t s);
+// Filter launchers: write the (mid, slope) pairs of every row (see fbp.h).
+cudaError_t launch_filter_direct(const Plan &p, const float *sino, int ld, void *q,
+                                 cudaStream_t s);
+cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q, cudaStream_t s);
 size_t filter_fft_smem_bytes(int N);
 size_t filter_direct_smem_bytes(int D);
-cudaError_t launch_backproject_f32(const Plan &p, const CUtensorMap &qmap, float *image,
-                                   cudaStream_t s);
+
+// Backprojection of one slice with its plan's launch shape.
+cudaError_t backproject_slice(const Plan &p, const void *q, float *image, cudaStream_t s);
+
 cudaError_t launch_radon_forward_f32(const Plan &p, const float *image, float *sino,
                                      cudaStream_t s);
 

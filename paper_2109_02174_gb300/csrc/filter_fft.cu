@@ -12,6 +12,7 @@
 // between two shared-memory buffers; twiddles exp(-2 pi i t / N) come from a
 // plan table computed in FP64.  The 1/N of the inverse is folded into H.
 #include "fbp_internal.h"
+#include "pairs.cuh"
 
 namespace fbp {
 namespace {
@@ -89,10 +90,11 @@ __device__ float2 *fft(float2 *x, float2 *y, const float2 *__restrict__ tw, int 
     return x;
 }
 
+template <typename OutT>
 __global__ void __launch_bounds__(256)
-    filter_fft_f32_kernel(const float *__restrict__ sino, int ld, const float2 *__restrict__ tw,
-                          const float *__restrict__ hspec, float *__restrict__ q, int A, int D,
-                          int pitch, int N, int log2n)
+    filter_fft_kernel(const float *__restrict__ sino, int ld, const float2 *__restrict__ tw,
+                      const float *__restrict__ hspec, OutT *__restrict__ q, int A, int D,
+                      int pitch, int N, int log2n)
 {
     extern __shared__ float2 buf[];
     float2 *x = buf;
@@ -118,12 +120,17 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     float2 *other = (z == x) ? y : x;
     z = fft(z, other, tw, N, log2n, true);
-    float *q0 = q + (size_t)i0 * pitch;
-    float *q1 = q + (size_t)(i0 + 1) * pitch;
-    for (int k = threadIdx.x; k < pitch; k += blockDim.x) {
-        const float2 v = (k < D) ? z[k] : make_float2(0.0f, 0.0f);
-        q0[k] = v.x;
-        if (two) q1[k] = v.y;
+    // z[k] = (Q_i0[k], Q_i0+1[k]) for k < n_det; write (mid, slope) pairs.
+    OutT *r0 = q + (size_t)i0 * pitch;
+    OutT *r1 = q + (size_t)(i0 + 1) * pitch;
+    for (int p = threadIdx.x; p < pitch / 2; p += blockDim.x) {
+        float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
+        if (p <= D) {
+            if (p >= 1) a = z[p - 1];
+            if (p < D) b = z[p];
+        }
+        store_pair(r0, p, a.x, b.x);
+        if (two) store_pair(r1, p, a.y, b.y);
     }
 }
 
@@ -131,18 +138,26 @@ __global__ void __launch_bounds__(256)
 
 size_t filter_fft_smem_bytes(int N) { return sizeof(float2) * (size_t)(2 * N); }
 
-cudaError_t launch_filter_fft_f32(const Plan &p, const float *sino, int ld, float *q,
-                                  cudaStream_t s)
+namespace {
+template <typename OutT>
+cudaError_t launch(const Plan &p, const float *sino, int ld, OutT *q, cudaStream_t s)
 {
     const size_t smem = filter_fft_smem_bytes(p.fft_len);
-    cudaError_t e = cudaFuncSetAttribute(filter_fft_f32_kernel,
+    cudaError_t e = cudaFuncSetAttribute(filter_fft_kernel<OutT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int log2n = 0;
     while ((1 << log2n) < p.fft_len) ++log2n;
-    filter_fft_f32_kernel<<<(p.A + 1) / 2, 256, smem, s>>>(sino, ld, p.d_fft_tw, p.d_fft_h, q,
-                                                          p.A, p.D, p.pitch, p.fft_len, log2n);
+    filter_fft_kernel<OutT><<<(p.A + 1) / 2, 256, smem, s>>>(sino, ld, p.d_fft_tw, p.d_fft_h, q,
+                                                            p.A, p.D, p.pitch, p.fft_len, log2n);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q, cudaStream_t s)
+{
+    if (p.q_storage == FBP_F16) return launch(p, sino, ld, static_cast<__half *>(q), s);
+    return launch(p, sino, ld, static_cast<float *>(q), s);
 }
 
 }  // namespace fbp

@@ -1,0 +1,164 @@
+"""GPU: batched reconstruction (one captured graph, one persistent launch per
+kernel configuration) is bit-identical to each slice reconstructed alone, and
+matches the FP64 oracle within the FP32 bars."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+MAX_REL = 1e-4
+RMSE_REL = 2e-5
+NTHREADS = 16
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_02174_gb300 import build
+    build.build()
+    import paper_2109_02174_gb300 as m
+    return m
+
+
+def _sino(spec):
+    import torch
+    return torch.from_numpy(synthetic.sinogram(spec).astype(np.float32)).cuda()
+
+
+def _alone(fbp, plan, sino):
+    import torch
+    img = plan.reconstruct(sino)
+    torch.cuda.synchronize()
+    return img.cpu().numpy()
+
+
+def _parity(got, sino_t, spec):
+    th = synthetic.default_angles(spec.n_angles)
+    ref = oracle.fbp(sino_t.double().cpu().numpy(), th, spec.tau, spec.filter, spec.n_pix,
+                     nthreads=NTHREADS)
+    scale = np.abs(ref).max()
+    e_max = np.abs(got - ref).max() / scale
+    e_rms = np.sqrt(np.mean((got - ref) ** 2)) / scale
+    assert e_max <= MAX_REL and e_rms <= RMSE_REL, f"max {e_max:.3e} rmse {e_rms:.3e}"
+
+
+def small_uneven_specs(count=12, seed=33):
+    rng = synthetic.SplitMix64(seed)
+    out = []
+    for s in range(count):
+        n = rng.choice((64, 96, 128, 200))
+        a = rng.choice((45, 90, 180, 360))
+        out.append(synthetic.SliceSpec(n, a, synthetic.det_for(n), 6, seed=500 + s,
+                                       filter=s % 2))
+    return out
+
+
+def test_batch_matches_alone_bitwise_and_oracle(fbp):
+    import torch
+    specs = small_uneven_specs()
+    plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det, filter=s.filter) for s in specs]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch(plans, sinos)
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.status()
+    for spec, plan, sino, img in zip(specs, plans, sinos, batch.images):
+        got = img.cpu().numpy()
+        assert np.array_equal(got, _alone(fbp, plan, sino)), spec
+        _parity(got.astype(np.float64), sino, spec)
+
+
+def test_batch_relaunch_sees_new_data(fbp):
+    import torch
+    specs = small_uneven_specs(5, seed=34)
+    plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det) for s in specs]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch(plans, sinos)
+    batch.launch()
+    first = [im.clone() for im in batch.images]
+    for s, t in zip(specs, sinos):
+        s2 = synthetic.SliceSpec(s.n_pix, s.n_angles, s.n_det, 6, seed=s.seed + 77)
+        t.copy_(_sino(s2))
+    batch.launch()
+    torch.cuda.synchronize()
+    for plan, sino, im, f in zip(plans, sinos, batch.images, first):
+        now = im.cpu().numpy()
+        assert not np.array_equal(now, f.cpu().numpy())
+        assert np.array_equal(now, _alone(fbp, plan, sino))
+
+
+def test_batch_mixes_kernel_configurations(fbp):
+    """Slices whose plans pick different kernels (tile shape, FP16 pairs, Kahan)
+    share one batch; each still equals its own alone result bit for bit."""
+    import torch
+    n, A = 96, 60
+    D = synthetic.det_for(n)
+    plans = [fbp.Plan(n, A, D), fbp.Plan(n, A, 2 * D, det_spacing=0.45),
+             fbp.Plan(n, A, D, q_storage=2), fbp.Plan(n, A, D, accumulate=1),
+             fbp.Plan(n, A, D, tile_x=8, tile_y=32)]
+    specs = [synthetic.SliceSpec(n, A, p.n_det, 5, seed=900 + i, tau=p.det_spacing)
+             for i, p in enumerate(plans)]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch(plans, sinos)
+    batch.launch()
+    torch.cuda.synchronize()
+    for plan, sino, img in zip(plans, sinos, batch.images):
+        assert np.array_equal(img.cpu().numpy(), _alone(fbp, plan, sino))
+
+
+def test_batched_uneven_workload_64(fbp):
+    """The batched configuration: 64 uneven slices (n in {256,384,512,768},
+    A in {180,360,720,1440}) in one graph.  Every slice is bit-identical to its
+    alone result; four slices, the largest among them, are checked against the
+    oracle at sampled pixels."""
+    import torch
+    specs = synthetic.cfg_batch()
+    plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det) for s in specs]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch(plans, sinos)
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.status()
+    imgs = [im.cpu().numpy() for im in batch.images]
+    for plan, sino, img in zip(plans, sinos, imgs):
+        assert np.array_equal(img, _alone(fbp, plan, sino))
+    big = max(range(64), key=lambda i: specs[i].updates)
+    for i in sorted({big, 0, 17, 42}):
+        s = specs[i]
+        th = synthetic.default_angles(s.n_angles)
+        Q = oracle.filter_rows(sinos[i].double().cpu().numpy(), s.filter, 1.0, nthreads=NTHREADS)
+        rng = np.random.default_rng(i)
+        rows = rng.integers(0, s.n_pix, 400)
+        cols = rng.integers(0, s.n_pix, 400)
+        ref = oracle.backproject_pixels(Q, th, 1.0, s.n_pix, rows, cols)
+        err = np.abs(imgs[i][rows, cols] - ref) / np.abs(ref).max()
+        assert err.max() <= MAX_REL and np.sqrt(np.mean(err ** 2)) <= RMSE_REL
+
+
+def test_batch_argument_errors(fbp):
+    import torch
+    plan = fbp.Plan(32, 8, 46)
+    s = torch.zeros(8, 46, device="cuda")
+    im = torch.zeros(32, 32, device="cuda")
+    ws = plan.empty_workspace()
+    good = fbp.fbp_batch_io(s.data_ptr(), 46, im.data_ptr(), ws.data_ptr())
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.fbp_batch_build([], [])
+    assert e.value.status == fbp.FBP_ERR_INVALID_ARG
+    bad = fbp.fbp_batch_io(s.data_ptr() + 4, 46, im.data_ptr(), ws.data_ptr())
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.fbp_batch_build([plan.handle], [bad])
+    assert e.value.status == fbp.FBP_ERR_ALIGNMENT
+    short = fbp.fbp_batch_io(s.data_ptr(), 40, im.data_ptr(), ws.data_ptr())
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.fbp_batch_build([plan.handle], [short])
+    assert e.value.status == fbp.FBP_ERR_INVALID_ARG
+    h = fbp.fbp_batch_build([plan.handle], [good])
+    fbp.fbp_batch_launch(h, 0)
+    fbp.fbp_batch_status(h)
+    fbp.fbp_batch_destroy(h)

@@ -40,6 +40,27 @@ def _np(t):
     return t.double().cpu().numpy()
 
 
+def to_pairs(Q, pitch, dtype=np.float32):
+    """Interpolation-ready rows: pair p = k + 1 holds ((Q[k]+Q[k+1])/2, Q[k+1]-Q[k]),
+    k = -1 .. D-1, Q zero outside [0, D); the rest of the row is zero."""
+    Q = np.asarray(Q, dtype=np.float64)
+    A, D = Q.shape
+    z = np.zeros((A, D + 2))
+    z[:, 1:D + 1] = Q
+    out = np.zeros((A, pitch), dtype=np.float64)
+    out[:, 0:2 * (D + 1):2] = 0.5 * (z[:, :-1] + z[:, 1:])
+    out[:, 1:2 * (D + 1):2] = z[:, 1:] - z[:, :-1]
+    return out.astype(dtype)
+
+
+def from_pairs(R, D):
+    """Q[k] for k = 0 .. D-1: the left end, mid - slope/2, of the segment in pair k + 1."""
+    R = np.asarray(R, dtype=np.float64)
+    mid = R[:, 2:2 * (D + 1):2]
+    slope = R[:, 3:2 * (D + 1):2]
+    return mid - 0.5 * slope
+
+
 def errors(got, ref):
     scale = float(np.abs(ref).max())
     return (float(np.abs(got - ref).max()) / scale,
@@ -64,9 +85,10 @@ def test_filter_matches_oracle(fbp, kind, path):
     assert plan.filter_path == PATHS[path]
     q = _np(plan.filter(_t(P)))
     assert q.shape == (A, plan.q_pitch) and plan.q_pitch % 8 == 0
-    assert np.all(q[:, D:] == 0.0)
+    assert np.all(q[:, 2 * (D + 1):] == 0.0)
     ref = oracle.filter_rows(P.astype(np.float64), kind, 1.0)
-    np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+    np.testing.assert_allclose(q, to_pairs(ref, plan.q_pitch, np.float64), rtol=0,
+                               atol=2e-6 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
@@ -77,7 +99,7 @@ def test_filter_respects_row_stride(fbp, path):
     plan = fbp.Plan(30, A, D, filter_path=PATHS[path])
     q = _np(plan.filter(big[:, :D]))
     ref = oracle.filter_rows(big[:, :D].double().cpu().numpy(), 0, 1.0)
-    np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
+    np.testing.assert_allclose(from_pairs(q, D), ref, rtol=0, atol=2e-6 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("D,fft_len", [(2899, 0), (4096, 8192), (725, 4096), (1, 0), (2, 16)])
@@ -89,8 +111,8 @@ def test_fft_filter_lengths(fbp, D, fft_len):
     assert plan.fft_len >= 2 * D - 1 and plan.fft_len & (plan.fft_len - 1) == 0
     q = _np(plan.filter(_t(P)))
     ref = oracle.filter_rows(P.astype(np.float64), 0, 1.0)
-    np.testing.assert_allclose(q[:, :D], ref, rtol=0, atol=2e-6 * np.abs(ref).max())
-    assert np.all(q[:, D:] == 0.0)
+    np.testing.assert_allclose(q, to_pairs(ref, plan.q_pitch, np.float64), rtol=0,
+                               atol=2e-6 * np.abs(ref).max())
 
 
 # ---------------------------------------------------------------- backprojection
@@ -105,10 +127,21 @@ def test_backproject_matches_oracle(fbp, n, A, D, tau):
     Q = rng.standard_normal((A, D)).astype(np.float32)
     th = oracle.default_angles(A)
     plan = fbp.Plan(n, A, D, det_spacing=tau)
-    qp = np.zeros((A, plan.q_pitch), dtype=np.float32)
-    qp[:, :D] = Q
-    got = _np(plan.backproject(_t(qp)))
+    got = _np(plan.backproject(_t(to_pairs(Q, plan.q_pitch))))
     ref = oracle.backproject(Q.astype(np.float64), th, tau, n, nthreads=NTHREADS)
+    assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("tile", [(32, 64), (32, 32), (8, 32)])
+def test_backproject_tile_shapes(fbp, tile):
+    """Every tile shape the plan can pick gives the same image within the bars."""
+    n, A = 100, 37
+    D = synthetic.det_for(n)
+    Q = np.random.default_rng(3).standard_normal((A, D)).astype(np.float32)
+    plan = fbp.Plan(n, A, D, tile_x=tile[0], tile_y=tile[1])
+    got = _np(plan.backproject(_t(to_pairs(Q, plan.q_pitch))))
+    ref = oracle.backproject(Q.astype(np.float64), oracle.default_angles(A), 1.0, n,
+                             nthreads=NTHREADS)
     assert_parity(got, ref)
 
 
@@ -119,9 +152,7 @@ def test_backproject_arbitrary_angles(fbp):
     th = np.sort(rng.uniform(-3.0, 7.0, A))
     Q = rng.standard_normal((A, D)).astype(np.float32)
     plan = fbp.Plan(n, A, D, angles=th)
-    qp = np.zeros((A, plan.q_pitch), dtype=np.float32)
-    qp[:, :D] = Q
-    got = _np(plan.backproject(_t(qp)))
+    got = _np(plan.backproject(_t(to_pairs(Q, plan.q_pitch))))
     ref = oracle.backproject(Q.astype(np.float64), th, 1.0, n, nthreads=NTHREADS)
     assert_parity(got, ref)
 
@@ -144,9 +175,7 @@ def test_constant_rows_give_pi_c(fbp):
     n, A = 64, 45
     D = synthetic.det_for(n)
     plan = fbp.Plan(n, A, D)
-    qp = np.zeros((A, plan.q_pitch), dtype=np.float32)
-    qp[:, :D] = 1.25
-    got = _np(plan.backproject(_t(qp)))
+    got = _np(plan.backproject(_t(to_pairs(np.full((A, D), 1.25), plan.q_pitch))))
     np.testing.assert_allclose(got, math.pi * 1.25, rtol=2e-6)
 
 
@@ -207,6 +236,31 @@ def test_large_slice_2048_sampled(fbp):
         f"max {err.max():.3e} rms {np.sqrt(np.mean(err ** 2)):.3e}"
 
 
+# ---------------------------------------------------------------- precision variants
+def test_kahan_accumulation_meets_fp32_bars(fbp):
+    """Kahan-compensated sum over angles (2048 x 2048-class angle count on a small image)."""
+    spec = synthetic.SliceSpec(256, 2048, synthetic.det_for(256), 10, seed=41)
+    e_max, e_rms = _check_slice(fbp, spec, accumulate=1)
+    assert e_max <= MAX_REL and e_rms <= RMSE_REL
+
+
+def test_fp16_pairs_error_is_stated(fbp):
+    """FP16-stored (mid, slope) pairs: no bar from the spec; the error is reported
+    and must stay in the range half precision allows (~1e-3 of max|f|)."""
+    import torch
+    spec = synthetic.cfg_plain()
+    th = synthetic.default_angles(spec.n_angles)
+    sino32 = synthetic.sinogram(spec, th).astype(np.float32)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, q_storage=2)
+    q = plan.filter(_t(sino32))
+    assert q.dtype == torch.float16
+    got = _np(plan.backproject(q))
+    ref = oracle.fbp(sino32.astype(np.float64), th, 1.0, 0, spec.n_pix, nthreads=NTHREADS)
+    e_max, e_rms = errors(got, ref)
+    print(f"fp16 pairs: max {e_max:.3e} rmse {e_rms:.3e} of max|f|")
+    assert e_max < 5e-3 and e_rms < 1e-3
+
+
 # ---------------------------------------------------------------- projector
 def test_radon_forward_matches_oracle(fbp):
     n, A = 57, 33
@@ -227,10 +281,8 @@ def test_gpu_adjoint_pair(fbp):
     x = rng.standard_normal((n, n)).astype(np.float32)
     y = rng.standard_normal((A, D)).astype(np.float32)
     plan = fbp.Plan(n, A, D, filter=2)
-    yp = np.zeros((A, plan.q_pitch), dtype=np.float32)
-    yp[:, :D] = y
     Rx = _np(plan.radon_forward(_t(x)))
-    By = _np(plan.backproject(_t(yp)))
+    By = _np(plan.backproject(_t(to_pairs(y, plan.q_pitch))))
     lhs = float(np.sum(Rx * y))
     rhs = (A / math.pi) * float(np.sum(x.astype(np.float64) * By))
     scale = float(np.sum(np.abs(Rx * y)))
