@@ -244,9 +244,23 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     fbp_options o;
     fbp_options_default(&o);
     if (opt != nullptr) o = *opt;
-    if (o.dtype != FBP_F32) {
+    if (o.dtype != FBP_F32 && o.dtype != FBP_F64) {
         set_error("fbp_plan: dtype %d not built", o.dtype);
         return FBP_ERR_UNSUPPORTED;
+    }
+    if (o.dtype == FBP_F64) {
+        // The FP64 path is the direct filter and a plain per-pixel backprojection.
+        if (o.q_storage != FBP_F32 || o.accumulate != FBP_ACC_PLAIN ||
+            (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT)) {
+            set_error("fbp_plan: FP64 plans take the default q_storage/accumulate and the "
+                      "direct filter");
+            return FBP_ERR_UNSUPPORTED;
+        }
+        if (filter_direct_f64_smem_bytes(n_det) > 200 * 1024) {
+            set_error("fbp_plan: n_det %d too large for the FP64 direct filter", n_det);
+            return FBP_ERR_UNSUPPORTED;
+        }
+        o.filter_path = FBP_PATH_DIRECT;
     }
     if ((o.q_storage != FBP_F32 && o.q_storage != FBP_F16) ||
         (o.accumulate != FBP_ACC_PLAIN && o.accumulate != FBP_ACC_KAHAN)) {
@@ -268,14 +282,15 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
                   2 * n_det - 1);
         return FBP_ERR_INVALID_ARG;
     }
-    const bool fft_ok = fft_len <= kMaxFftLen;
+    const bool fft_ok = fft_len <= kMaxFftLen && o.dtype == FBP_F32;
     int path = o.filter_path;
     if (path == FBP_PATH_AUTO) path = fft_ok ? FBP_PATH_FFT : FBP_PATH_DIRECT;
     if (path == FBP_PATH_FFT && !fft_ok) {
         set_error("fbp_plan: FFT length %d exceeds %d", fft_len, kMaxFftLen);
         return FBP_ERR_UNSUPPORTED;
     }
-    if (path == FBP_PATH_DIRECT && filter_direct_smem_bytes(n_det) > 200 * 1024) {
+    if (path == FBP_PATH_DIRECT && o.dtype == FBP_F32 &&
+        filter_direct_smem_bytes(n_det) > 200 * 1024) {
         set_error("fbp_plan: n_det %d too large for the direct filter", n_det);
         return FBP_ERR_UNSUPPORTED;
     }
@@ -324,6 +339,7 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         if ((o.tile_x || o.tile_y) && (o.tile_x != tx || o.tile_y != ty)) continue;
         if (window_pairs(trig, tx, ty, align) <= 128) pick = k;
     }
+    if (pick < 0 && o.dtype == FBP_F64) pick = 0;  // the FP64 path has no tiles
     if (pick < 0) {
         delete p;
         set_error("fbp_plan: no backprojection tile fits the detector window (det_spacing %.3g, "
@@ -432,11 +448,14 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
         set_error("fbp_filter: ld_sino %d < n_det %d", ld_sino, p->D);
         return FBP_ERR_INVALID_ARG;
     }
-    cudaError_t e =
-        (p->filter_path == FBP_PATH_FFT)
-            ? launch_filter_fft(*p, static_cast<const float *>(sino), ld_sino, filtered, stream)
-            : launch_filter_direct(*p, static_cast<const float *>(sino), ld_sino, filtered,
-                                   stream);
+    cudaError_t e;
+    if (p->dtype == FBP_F64)
+        e = launch_filter_direct_f64(*p, static_cast<const double *>(sino), ld_sino,
+                                     static_cast<double *>(filtered), stream);
+    else if (p->filter_path == FBP_PATH_FFT)
+        e = launch_filter_fft(*p, static_cast<const float *>(sino), ld_sino, filtered, stream);
+    else
+        e = launch_filter_direct(*p, static_cast<const float *>(sino), ld_sino, filtered, stream);
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_filter");
 }
 
@@ -446,6 +465,11 @@ fbp_status fbp_backproject(fbp_plan_t plan, const void *filtered, void *image,
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     fbp_status st = check_call(p, "fbp_backproject", {filtered, image});
     if (st != FBP_OK) return st;
+    if (p->dtype == FBP_F64) {
+        cudaError_t e = launch_backproject_f64(*p, static_cast<const double *>(filtered),
+                                               static_cast<double *>(image), stream);
+        return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_backproject");
+    }
     cudaError_t e = backproject_slice(*p, filtered, static_cast<float *>(image), stream);
     if (e == cudaErrorInvalidValue) return FBP_ERR_CUDA;  // tensor map encoding (message set)
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_backproject");
@@ -467,6 +491,10 @@ fbp_status radon_forward(fbp_plan_t plan, const void *image, void *sino, fbp_str
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     fbp_status st = check_call(p, "radon_forward", {image, sino});
     if (st != FBP_OK) return st;
+    if (p->dtype != FBP_F32) {
+        set_error("radon_forward: FP32 plans only");
+        return FBP_ERR_UNSUPPORTED;
+    }
     cudaError_t e = launch_radon_forward_f32(*p, static_cast<const float *>(image),
                                              static_cast<float *>(sino), stream);
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "radon_forward");

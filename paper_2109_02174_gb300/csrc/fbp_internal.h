@@ -44,7 +44,10 @@ struct Plan {
 };
 
 // Element size of the filtered sinogram.
-inline int q_elem_bytes(const Plan &p) { return p.q_storage == FBP_F16 ? 2 : 4; }
+inline int q_elem_bytes(const Plan &p)
+{
+    return p.dtype == FBP_F64 ? 8 : (p.q_storage == FBP_F16 ? 2 : 4);
+}
 
 // Thread-local error message for fbp_last_error().
 void set_error(const char *fmt, ...);
@@ -62,6 +65,12 @@ size_t filter_direct_smem_bytes(int D);
 
 // Backprojection of one slice with its plan's launch shape.
 cudaError_t backproject_slice(const Plan &p, const void *q, float *image, cudaStream_t s);
+
+// FP64 path (fp64.cu).
+cudaError_t launch_filter_direct_f64(const Plan &p, const double *sino, int ld, double *q,
+                                     cudaStream_t s);
+cudaError_t launch_backproject_f64(const Plan &p, const double *q, double *image, cudaStream_t s);
+size_t filter_direct_f64_smem_bytes(int D);
 
 cudaError_t launch_radon_forward_f32(const Plan &p, const float *image, float *sino,
                                      cudaStream_t s);

@@ -261,6 +261,46 @@ def test_fp16_pairs_error_is_stated(fbp):
     assert e_max < 5e-3 and e_rms < 1e-3
 
 
+# ---------------------------------------------------------------- FP64 path
+FP64_REL = 1e-10
+
+
+def _fp64_slice(fbp, spec):
+    import torch
+    th = synthetic.default_angles(spec.n_angles)
+    sino = synthetic.sinogram(spec, th)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter, dtype=1)
+    assert plan.dtype == torch.float64
+    got = plan.reconstruct(torch.from_numpy(sino).cuda())
+    torch.cuda.synchronize()
+    plan.device_status()
+    ref = oracle.fbp(sino, th, 1.0, spec.filter, spec.n_pix, nthreads=NTHREADS)
+    return errors(got.cpu().numpy(), ref)
+
+
+def test_fp64_float_double_slice_512(fbp):
+    """The float-vs-double configuration on the FP64 GPU path: <= 1e-10 of max|f|."""
+    e_max, e_rms = _fp64_slice(fbp, synthetic.cfg_float_double())
+    print(f"fp64: max {e_max:.3e} rmse {e_rms:.3e}")
+    assert e_max <= FP64_REL
+
+
+@pytest.mark.parametrize("n,A,D", [(3, 2, 5), (33, 17, 40), (70, 21, 60)])
+def test_fp64_small_and_ragged(fbp, n, A, D):
+    spec = synthetic.SliceSpec(n, A, D, 4, seed=n + A, filter=0)
+    e_max, _ = _fp64_slice(fbp, spec)
+    assert e_max <= FP64_REL
+
+
+def test_fp64_rejects_fp32_only_options(fbp):
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.Plan(64, 10, 91, dtype=1, filter_path=2)
+    assert e.value.status == fbp.FBP_ERR_UNSUPPORTED
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.Plan(64, 10, 91, dtype=1, q_storage=2)
+    assert e.value.status == fbp.FBP_ERR_UNSUPPORTED
+
+
 # ---------------------------------------------------------------- projector
 def test_radon_forward_matches_oracle(fbp):
     n, A = 57, 33
