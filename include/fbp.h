@@ -189,6 +189,17 @@ typedef struct {
 fbp_status fbp_batch_build(fbp_batch_t *out, const fbp_plan_t *plans, int n,
                            const fbp_batch_io *io, fbp_stream_t stream);
 
+/*
+ * The same multi-slice work enqueued directly on `stream` (no graph): every
+ * slice's filter, then one persistent backprojection launch per kernel
+ * configuration over all tiles.  For work lists that change call to call
+ * (the serving loop); allocates nothing.  Images are bit-identical to
+ * fbp_reconstruct per slice.  A device timeout is recorded in the status word
+ * of plans[0].
+ */
+fbp_status fbp_reconstruct_many(const fbp_plan_t *plans, int n, const fbp_batch_io *io,
+                                fbp_stream_t stream);
+
 /* Parts of a batch graph (fbp_batch_build records both). */
 enum { FBP_BATCH_FILTER = 1, FBP_BATCH_BACKPROJECT = 2 };
 
@@ -217,6 +228,59 @@ fbp_status fbp_batch_status(fbp_batch_t batch);
 
 /* Release the batch (synchronises the device).  NULL is a no-op. */
 fbp_status fbp_batch_destroy(fbp_batch_t batch);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop for slice reconstructions that arrive over time (the paper's
+ * motivation, section "Introduction": a shorter wait for the exam result).
+ * A worker thread admits queued requests in arrival order while a device
+ * arena of hbm_budget_bytes can hold their sinogram, filtered pairs and image,
+ * and launches admitted requests as waves (copies in, every slice's filter,
+ * one persistent backprojection over all their tiles, copies out) on up to
+ * n_streams streams at once, so requests that arrive while others run are
+ * batched and overlap on the device (continuous batching).  Each request's
+ * image is bit-identical to fbp_reconstruct with a default plan of its
+ * geometry.  Latency = submit to the end of its image copy. */
+typedef struct fbp_server_s *fbp_server_t;
+
+typedef struct {
+    int n_pix, n_angles, n_det;
+    double det_spacing;
+    int filter;             /* fbp_filter_type */
+    const float *host_sino; /* host [n_angles][n_det]; must stay valid until the request is done */
+    float *host_image;      /* host [n_pix][n_pix]; written when done (pin both for async copies) */
+} fbp_request;
+
+typedef struct {
+    long long submitted, completed, failed, admission_stalls, waves;
+    int max_waves_in_flight;                /* > 1: waves overlapped on the device */
+    double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed requests */
+    double span_s;                          /* first submit to last completion */
+    size_t bytes_in_use, peak_bytes, budget_bytes;
+} fbp_server_stats;
+
+/* Start a server on the current device: reserves hbm_budget_bytes (>= 1 MiB)
+ * of device memory up front; max_wave 1..64 requests per wave; n_streams 1..16. */
+fbp_status fbp_server_create(fbp_server_t *out, size_t hbm_budget_bytes, int max_wave,
+                             int n_streams);
+/* Create the plan of a geometry ahead of traffic (plan creation synchronises the device). */
+fbp_status fbp_server_warm(fbp_server_t server, int n_pix, int n_angles, int n_det,
+                           double det_spacing, int filter);
+/* Queue a request; *id identifies it.  FBP_ERR_INVALID_ARG for a bad geometry or
+ * NULL buffer, FBP_ERR_BUDGET if it alone exceeds the budget.  Never blocks on the GPU. */
+fbp_status fbp_server_submit(fbp_server_t server, const fbp_request *req, long long *id);
+/* Withdraw a request that is still queued (not yet admitted). */
+fbp_status fbp_server_cancel(fbp_server_t server, long long id);
+/* Block until the request is done; FBP_ERR_TIMEOUT after timeout_s seconds. */
+fbp_status fbp_server_wait(fbp_server_t server, long long id, double timeout_s);
+/* state: 0 queued, 1 admitted, 2 running, 3 done, 4 failed, 5 cancelled;
+ * latency_ms: submit to completion, or -1 if not done.  Either may be NULL. */
+fbp_status fbp_server_request_info(fbp_server_t server, long long id, int *state,
+                                   double *latency_ms);
+/* Block until nothing is queued or running; FBP_ERR_TIMEOUT after timeout_s. */
+fbp_status fbp_server_drain(fbp_server_t server, double timeout_s);
+fbp_status fbp_server_get_stats(fbp_server_t server, fbp_server_stats *out);
+/* Stop the worker, wait for the streams, release plans and the arena. NULL is a no-op. */
+fbp_status fbp_server_destroy(fbp_server_t server);
 
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)

@@ -39,6 +39,25 @@ class fbp_batch_io(ctypes.Structure):
                 ("image", ctypes.c_void_p), ("workspace", ctypes.c_void_p)]
 
 
+class fbp_request(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_det", ctypes.c_int),
+                ("det_spacing", ctypes.c_double), ("filter", ctypes.c_int),
+                ("host_sino", ctypes.c_void_p), ("host_image", ctypes.c_void_p)]
+
+
+class fbp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("admission_stalls", ctypes.c_longlong),
+                ("waves", ctypes.c_longlong), ("max_waves_in_flight", ctypes.c_int),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("span_s", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class fbp_options(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in
                 ("dtype", "q_storage", "accumulate", "filter_path", "fft_len",
@@ -69,6 +88,17 @@ _SIGS = {
     "fbp_batch_build_parts": [ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                               ctypes.POINTER(fbp_batch_io), _I, _P],
     "fbp_batch_launch": [_P, _P],
+    "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
+    "fbp_server_create": [ctypes.POINTER(_P), ctypes.c_size_t, _I, _I],
+    "fbp_server_warm": [_P, _I, _I, _I, ctypes.c_double, _I],
+    "fbp_server_submit": [_P, ctypes.POINTER(fbp_request), ctypes.POINTER(ctypes.c_longlong)],
+    "fbp_server_cancel": [_P, ctypes.c_longlong],
+    "fbp_server_wait": [_P, ctypes.c_longlong, ctypes.c_double],
+    "fbp_server_request_info": [_P, ctypes.c_longlong, ctypes.POINTER(_I),
+                                ctypes.POINTER(ctypes.c_double)],
+    "fbp_server_drain": [_P, ctypes.c_double],
+    "fbp_server_get_stats": [_P, ctypes.POINTER(fbp_server_stats)],
+    "fbp_server_destroy": [_P],
     "fbp_batch_run_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "fbp_batch_status": [_P],
     "fbp_batch_destroy": [_P],
@@ -183,6 +213,12 @@ def fbp_batch_build(plans, ios, parts: int = FBP_BATCH_FILTER | FBP_BATCH_BACKPR
     h = _P()
     _check(load_library().fbp_batch_build_parts(ctypes.byref(h), parr, n, iarr, int(parts), None))
     return h.value
+
+
+def fbp_reconstruct_many(plans, ios, stream: int):
+    n = len(plans)
+    _check(load_library().fbp_reconstruct_many((_P * n)(*plans), n, (fbp_batch_io * n)(*ios),
+                                               stream))
 
 
 def fbp_batch_run_host(batch: int, host_sino_ptrs, host_image_ptrs, stream: int):
@@ -321,6 +357,70 @@ class Batch:
         if getattr(self, "handle", None):
             fbp_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching reconstruction server (fbp_server_* in libfbp).
+
+    submit() takes host tensors (pin them: the copies are asynchronous) that
+    must stay alive until the request is done.
+    """
+
+    QUEUED, ADMITTED, RUNNING, DONE, FAILED, CANCELLED = range(6)
+
+    def __init__(self, hbm_budget_bytes: int, max_wave: int = 32, n_streams: int = 2):
+        h = _P()
+        _check(load_library().fbp_server_create(ctypes.byref(h), int(hbm_budget_bytes),
+                                                int(max_wave), int(n_streams)))
+        self.handle = h.value
+        self._keep = {}
+
+    def warm(self, n_pix, n_angles, n_det, det_spacing=1.0, filter=FBP_FILTER_RAM_LAK):
+        _check(load_library().fbp_server_warm(self.handle, int(n_pix), int(n_angles),
+                                              int(n_det), float(det_spacing), int(filter)))
+
+    def submit(self, sino, image, n_pix, det_spacing=1.0, filter=FBP_FILTER_RAM_LAK) -> int:
+        assert sino.is_contiguous() and image.is_contiguous()
+        r = fbp_request(int(n_pix), int(sino.shape[0]), int(sino.shape[1]), float(det_spacing),
+                        int(filter), _ptr(sino), _ptr(image))
+        rid = ctypes.c_longlong()
+        _check(load_library().fbp_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)))
+        self._keep[rid.value] = (sino, image)
+        return rid.value
+
+    def cancel(self, rid: int):
+        _check(load_library().fbp_server_cancel(self.handle, int(rid)))
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        _check(load_library().fbp_server_wait(self.handle, int(rid), float(timeout_s)))
+        self._keep.pop(rid, None)
+
+    def info(self, rid: int):
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        _check(load_library().fbp_server_request_info(self.handle, int(rid), ctypes.byref(st),
+                                                      ctypes.byref(lat)))
+        return st.value, lat.value
+
+    def drain(self, timeout_s: float = 120.0):
+        _check(load_library().fbp_server_drain(self.handle, float(timeout_s)))
+
+    def stats(self) -> dict:
+        out = fbp_server_stats()
+        _check(load_library().fbp_server_get_stats(self.handle, ctypes.byref(out)))
+        return out.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fbp_check = load_library().fbp_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+            _check(fbp_check)
 
     def __del__(self):
         try:

@@ -144,8 +144,9 @@ cudaError_t backproject_slice(const Plan &p, const void *q, float *image, cudaSt
     std::memset(&L, 0, sizeof L);
     if (!encode_pairs_map(p, q, &L.maps[0])) return cudaErrorInvalidValue;
     L.slices[0] = slice_desc(p, image);
-    L.items = nullptr;
+    L.n_slices = 1;
     L.n_items = tiles_of(p);
+    L.tile_end[0] = L.n_items;
     L.wp_max = p.bp_wp;
     L.status = p.d_status;
     return launch_backproject(L, bp_config(p), s);

@@ -8,7 +8,7 @@
 //
 // Persistent, warp-specialised kernel.  The launch owns a list of work items,
 // each one TX x TY pixel tile of one slice (one launch may hold many slices of
-// different sizes); CTA b takes items b, b + grid, b + 2 grid, ...
+// different sizes; see BpLaunch); CTA b takes items b, b + grid, b + 2 grid, ...
 //   - warp NCW (the producer) walks the items' angle chunks: for each angle
 //     its lanes compute, in FP64, the first pair of the detector window the
 //     tile touches and the tile-local coordinate offset; lane 0 then issues
@@ -92,6 +92,18 @@ struct Layout {
     }
 };
 
+// Work item -> (slice, tile) through the prefix sums of the slices' tile counts.
+template <int MAXS>
+__device__ __forceinline__ int2 item_of(const BpLaunch<MAXS> &P, int item)
+{
+    int lo = 0, hi = P.n_slices - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (item < P.tile_end[mid]) hi = mid; else lo = mid + 1;
+    }
+    return make_int2(lo, item - (lo > 0 ? P.tile_end[lo - 1] : 0));
+}
+
 template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
 __global__ void __launch_bounds__(32 * (WX * WY + 1))
     bp_persistent_kernel(const __grid_constant__ BpLaunch<MAXS> P)
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
         // ------------------------------------------------------------ producer
         uint32_t it = 0;
         for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
-            const int2 wi = P.items ? P.items[item] : make_int2(0, item);
+            const int2 wi = item_of(P, item);
             const BpSlice &S = P.slices[wi.x];
             const CUtensorMap *map = &P.maps[wi.x];
             const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
 
     uint32_t it = 0;
     for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
-        const int2 wi = P.items ? P.items[item] : make_int2(0, item);
+        const int2 wi = item_of(P, item);
         const BpSlice &S = P.slices[wi.x];
         const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
         const int nch = (S.A + CH - 1) / CH;

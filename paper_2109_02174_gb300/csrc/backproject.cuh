@@ -25,15 +25,18 @@ struct BpSlice {
 };
 
 // Kernel parameters: one tensor map per slice (over that slice's filtered
-// pairs [A][pitch]) and the work list.  items == nullptr means a single slice
-// whose items are its tiles 0 .. n_items-1 in order.
+// pairs [A][pitch]) and the work list, implicit in the slice order: item j
+// is tile j - tile_end[s-1] of the slice s with tile_end[s-1] <= j < tile_end[s].
+// The host orders slices by angle count, most first, so the costliest tiles
+// are handed out first.
 template <int MAXS>
 struct BpLaunch {
     CUtensorMap maps[MAXS];
     BpSlice slices[MAXS];
-    const int2 *items;  // (slice, tile) in schedule order
-    int n_items;
-    int wp_max;  // largest wp over the slices (sizes the shared-memory rows)
+    int tile_end[MAXS];  // inclusive prefix sums of the slices' tile counts
+    int n_slices;
+    int n_items;  // = tile_end[n_slices - 1]
+    int wp_max;   // largest wp over the slices (sizes the shared-memory rows)
     int *status;
 };
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <tuple>
 #include <vector>
 
@@ -26,7 +27,6 @@ struct fbp_batch_s {
     int n;
     std::vector<const Plan *> plans;
     std::vector<fbp_batch_io> io;
-    std::vector<int2 *> d_items;  // one work list per kernel configuration
     int *d_status;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -41,50 +41,94 @@ void free_batch(fbp_batch_s *b)
     if (b == nullptr) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (int2 *p : b->d_items) cudaFree(p);
     cudaFree(b->d_status);
     delete b;
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Enqueue the batch on stream s (used once, under stream capture).
-cudaError_t enqueue(fbp_batch_s *b, cudaStream_t s,
-                    const std::vector<std::vector<int>> &groups,
-                    const std::vector<std::vector<int2>> &items)
+}  // namespace
+
+namespace fbp {
+
+// Every slice's filter, then one persistent backprojection launch per kernel
+// configuration over the tiles of all slices of that configuration (slices
+// with the most angles first).  Launch-only: no allocation, no synchronisation.
+cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
+                         int *status, cudaStream_t s)
 {
-    for (int i = 0; i < b->n && (b->parts & FBP_BATCH_FILTER); ++i) {
-        const Plan &p = *b->plans[(size_t)i];
-        const fbp_batch_io &io = b->io[(size_t)i];
+    for (int i = 0; i < n && (parts & FBP_BATCH_FILTER); ++i) {
+        const Plan &p = *plans[i];
         cudaError_t e = (p.filter_path == FBP_PATH_FFT)
-                            ? launch_filter_fft(p, static_cast<const float *>(io.sino),
-                                                io.ld_sino, io.workspace, s)
-                            : launch_filter_direct(p, static_cast<const float *>(io.sino),
-                                                   io.ld_sino, io.workspace, s);
+                            ? launch_filter_fft(p, static_cast<const float *>(io[i].sino),
+                                                io[i].ld_sino, io[i].workspace, s)
+                            : launch_filter_direct(p, static_cast<const float *>(io[i].sino),
+                                                   io[i].ld_sino, io[i].workspace, s);
         if (e != cudaSuccess) return e;
     }
-    for (size_t g = 0; g < groups.size() && (b->parts & FBP_BATCH_BACKPROJECT); ++g) {
-        BpLaunch<kBpMaxSlices> L;
-        std::memset(&L, 0, sizeof L);
-        const std::vector<int> &members = groups[g];
+    if (!(parts & FBP_BATCH_BACKPROJECT)) return cudaSuccess;
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_cfg;
+    for (int i = 0; i < n; ++i) {
+        const BpConfig c = bp_config(*plans[i]);
+        by_cfg[std::make_tuple(c.wx, c.wy, (int)c.half_pairs, (int)c.kahan)].push_back(i);
+    }
+    std::unique_ptr<BpLaunch<kBpMaxSlices>> L(new BpLaunch<kBpMaxSlices>());
+    for (auto &kv : by_cfg) {
+        std::vector<int> members = kv.second;
+        std::stable_sort(members.begin(), members.end(),
+                         [&](int a, int c) { return plans[a]->A > plans[c]->A; });
+        std::memset(L.get(), 0, sizeof(*L));
+        int acc = 0;
         for (size_t m = 0; m < members.size(); ++m) {
             const int i = members[m];
-            const Plan &p = *b->plans[(size_t)i];
-            if (!encode_pairs_map(p, b->io[(size_t)i].workspace, &L.maps[m]))
-                return cudaErrorInvalidValue;
-            L.slices[m] = slice_desc(p, static_cast<float *>(b->io[(size_t)i].image));
-            L.wp_max = std::max(L.wp_max, p.bp_wp);
+            const Plan &p = *plans[i];
+            if (!encode_pairs_map(p, io[i].workspace, &L->maps[m])) return cudaErrorInvalidValue;
+            L->slices[m] = slice_desc(p, static_cast<float *>(io[i].image));
+            acc += tiles_of(p);
+            L->tile_end[m] = acc;
+            L->wp_max = std::max(L->wp_max, p.bp_wp);
         }
-        L.items = b->d_items[g];
-        L.n_items = (int)items[g].size();
-        L.status = b->d_status;
-        cudaError_t e = launch_backproject_batch(L, bp_config(*b->plans[(size_t)members[0]]), 0, s);
+        L->n_slices = (int)members.size();
+        L->n_items = acc;
+        L->status = status;
+        cudaError_t e = launch_backproject_batch(*L, bp_config(*plans[members[0]]), 0, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-}  // namespace
+// Host-side checks shared by the batch calls.
+fbp_status check_many(const char *fn, const fbp_plan_t *plans, int n, const fbp_batch_io *io,
+                      int dev)
+{
+    if (plans == nullptr || io == nullptr || n < 1 || n > kBpMaxSlices) {
+        set_error("%s: need 1..%d slices with plans and buffers (got %d)", fn, kBpMaxSlices, n);
+        return FBP_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i) {
+        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+        const fbp_batch_io &b = io[i];
+        if (p == nullptr || p->device != dev) {
+            set_error("%s: slice %d: NULL plan or plan of another device", fn, i);
+            return FBP_ERR_INVALID_ARG;
+        }
+        if (p->dtype != FBP_F32) {
+            set_error("%s: slice %d: only FP32 plans batch", fn, i);
+            return FBP_ERR_UNSUPPORTED;
+        }
+        if (!b.sino || !b.image || !b.workspace || b.ld_sino < p->D) {
+            set_error("%s: slice %d: NULL buffer or ld_sino < n_det", fn, i);
+            return FBP_ERR_INVALID_ARG;
+        }
+        if (!aligned16(b.sino) || !aligned16(b.image) || !aligned16(b.workspace)) {
+            set_error("%s: slice %d: buffer not 16-byte aligned", fn, i);
+            return FBP_ERR_ALIGNMENT;
+        }
+    }
+    return FBP_OK;
+}
+
+}  // namespace fbp
 
 extern "C" {
 
@@ -107,36 +151,13 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
         return FBP_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (plans == nullptr || io == nullptr || n < 1 || n > kBpMaxSlices) {
-        set_error("fbp_batch_build: need 1..%d slices with plans and buffers (got %d)",
-                  kBpMaxSlices, n);
-        return FBP_ERR_INVALID_ARG;
-    }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         set_error("fbp_batch_build: no current CUDA device");
         return FBP_ERR_CUDA;
     }
-    for (int i = 0; i < n; ++i) {
-        const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
-        const fbp_batch_io &b = io[i];
-        if (p == nullptr || p->device != dev) {
-            set_error("fbp_batch_build: slice %d: NULL plan or plan of another device", i);
-            return FBP_ERR_INVALID_ARG;
-        }
-        if (p->dtype != FBP_F32) {
-            set_error("fbp_batch_build: slice %d: only FP32 plans batch", i);
-            return FBP_ERR_UNSUPPORTED;
-        }
-        if (!b.sino || !b.image || !b.workspace || b.ld_sino < p->D) {
-            set_error("fbp_batch_build: slice %d: NULL buffer or ld_sino < n_det", i);
-            return FBP_ERR_INVALID_ARG;
-        }
-        if (!aligned16(b.sino) || !aligned16(b.image) || !aligned16(b.workspace)) {
-            set_error("fbp_batch_build: slice %d: buffer not 16-byte aligned", i);
-            return FBP_ERR_ALIGNMENT;
-        }
-    }
+    fbp_status st = check_many("fbp_batch_build", plans, n, io, dev);
+    if (st != FBP_OK) return st;
 
     fbp_batch_s *b = new fbp_batch_s();
     b->device = dev;
@@ -151,54 +172,8 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
         b->io.push_back(io[i]);
         b->updates += (long long)b->plans.back()->n * b->plans.back()->n * b->plans.back()->A;
     }
-
-    // Group slices by kernel configuration; one work list per group, tiles of
-    // the slices with the most angles first (every tile of a slice costs the same).
-    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_cfg;
-    for (int i = 0; i < n; ++i) {
-        const BpConfig c = bp_config(*b->plans[(size_t)i]);
-        by_cfg[std::make_tuple(c.wx, c.wy, (int)c.half_pairs, (int)c.kahan)].push_back(i);
-    }
-    std::vector<std::vector<int>> groups;
-    std::vector<std::vector<int2>> items;
-    for (auto &kv : by_cfg) {
-        std::vector<int> members = kv.second;
-        std::stable_sort(members.begin(), members.end(), [&](int a, int c) {
-            const Plan &pa = *b->plans[(size_t)a], &pc = *b->plans[(size_t)c];
-            return pa.A > pc.A;
-        });
-        std::vector<int2> list;
-        // interleave slices of equal angle count tile by tile
-        size_t i0 = 0;
-        while (i0 < members.size()) {
-            size_t i1 = i0;
-            while (i1 < members.size() &&
-                   b->plans[(size_t)members[i1]]->A == b->plans[(size_t)members[i0]]->A)
-                ++i1;
-            int max_tiles = 0;
-            for (size_t m = i0; m < i1; ++m)
-                max_tiles = std::max(max_tiles, tiles_of(*b->plans[(size_t)members[m]]));
-            for (int t = 0; t < max_tiles; ++t)
-                for (size_t m = i0; m < i1; ++m)
-                    if (t < tiles_of(*b->plans[(size_t)members[m]]))
-                        list.push_back(make_int2((int)m, t));
-            i0 = i1;
-        }
-        groups.push_back(members);
-        items.push_back(list);
-    }
-
     cudaError_t e = cudaMalloc(&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
-    for (size_t g = 0; g < items.size() && e == cudaSuccess; ++g) {
-        int2 *d = nullptr;
-        e = cudaMalloc(&d, sizeof(int2) * items[g].size());
-        if (e == cudaSuccess) {
-            b->d_items.push_back(d);
-            e = cudaMemcpy(d, items[g].data(), sizeof(int2) * items[g].size(),
-                           cudaMemcpyHostToDevice);
-        }
-    }
     if (e != cudaSuccess) {
         free_batch(b);
         set_error("fbp_batch_build: %s", cudaGetErrorString(e));
@@ -210,7 +185,7 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t le = enqueue(b, cs, groups, items);
+        cudaError_t le = enqueue_many(b->plans.data(), b->io.data(), n, parts, b->d_status, cs);
         cudaError_t ee = cudaStreamEndCapture(cs, &b->graph);
         e = (le != cudaSuccess) ? le : ee;
     }
@@ -223,6 +198,28 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
     }
     (void)stream;
     *out = reinterpret_cast<fbp_batch_t>(b);
+    return FBP_OK;
+}
+
+fbp_status fbp_reconstruct_many(const fbp_plan_t *plans, int n, const fbp_batch_io *io,
+                                fbp_stream_t stream)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_error("fbp_reconstruct_many: no current CUDA device");
+        return FBP_ERR_CUDA;
+    }
+    fbp_status st = check_many("fbp_reconstruct_many", plans, n, io, dev);
+    if (st != FBP_OK) return st;
+    std::vector<const Plan *> ps((size_t)n);
+    for (int i = 0; i < n; ++i) ps[(size_t)i] = reinterpret_cast<const Plan *>(plans[i]);
+    cudaError_t e = enqueue_many(ps.data(), io, n, FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT,
+                                 ps[0]->d_status, stream);
+    if (e == cudaErrorInvalidValue) return FBP_ERR_CUDA;  // tensor map (message set)
+    if (e != cudaSuccess) {
+        set_error("fbp_reconstruct_many: %s", cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
+    }
     return FBP_OK;
 }
 
