@@ -8,6 +8,7 @@
 
 #include "backproject.cuh"
 #include "fbp_internal.h"
+#include "filter_tc.cuh"
 
 namespace fbp {
 
@@ -174,6 +175,11 @@ namespace {
 void free_plan(Plan *p)
 {
     if (p == nullptr) return;
+    if (p->tc) {
+        cudaFree(p->tc->d_hi);
+        cudaFree(p->tc->d_lo);
+        delete p->tc;
+    }
     cudaFree(p->d_trig64);
     cudaFree(p->d_taps32);
     cudaFree(p->d_taps64);
@@ -199,6 +205,61 @@ void make_taps(int kind, int D, double tau, std::vector<double> &out)
             h = (m == 0) ? 1.0 / tau : 0.0;
         out[(size_t)(m + D - 1)] = tau * h;
     }
+}
+
+// T[n][k] = tau h(n - k), split into tf32 hi (round to nearest, ties away) and
+// the FP32 remainder, rows n < D with stride kpad; plus their TMA maps.
+bool make_tc_tables(const Plan &p, const std::vector<double> &taps, TcTables *t)
+{
+    const int D = p.D;
+    t->kpad = round_up(D, 4);
+    const size_t count = (size_t)D * (size_t)t->kpad;
+    std::vector<float> hi(count, 0.0f), lo(count, 0.0f);
+    for (int n = 0; n < D; ++n) {
+        for (int k = 0; k < D; ++k) {
+            const double v = taps[(size_t)(n - k + D - 1)];
+            const float f = (float)v;
+            uint32_t b;
+            std::memcpy(&b, &f, 4);
+            b = (b + 0x1000u) & 0xFFFFE000u;
+            float h;
+            std::memcpy(&h, &b, 4);
+            hi[(size_t)n * t->kpad + k] = h;
+            lo[(size_t)n * t->kpad + k] = (float)(v - (double)h);
+        }
+    }
+    if (cudaMalloc(&t->d_hi, sizeof(float) * count) != cudaSuccess ||
+        cudaMalloc(&t->d_lo, sizeof(float) * count) != cudaSuccess) {
+        set_error("fbp_plan: cudaMalloc of the Toeplitz tables failed");
+        return false;
+    }
+    if (cudaMemcpy(t->d_hi, hi.data(), sizeof(float) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(t->d_lo, lo.data(), sizeof(float) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        set_error("fbp_plan: upload of the Toeplitz tables failed");
+        return false;
+    }
+    EncodeTiledFn enc = encode_fn();
+    if (enc == nullptr) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return false;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)D};
+    const cuuint64_t strides[1] = {(cuuint64_t)t->kpad * 4u};
+    const cuuint32_t box[2] = {32u, 128u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    for (int w = 0; w < 2; ++w) {
+        CUresult r = enc(w ? &t->t_lo : &t->t_hi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                         w ? t->d_lo : t->d_hi, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled (Toeplitz tables) failed (%d)", (int)r);
+            return false;
+        }
+    }
+    return true;
 }
 
 }  // namespace
@@ -269,8 +330,13 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         return FBP_ERR_UNSUPPORTED;
     }
     if (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT &&
-        o.filter_path != FBP_PATH_FFT) {
+        o.filter_path != FBP_PATH_FFT && o.filter_path != FBP_PATH_TOEPLITZ_TC) {
         set_error("fbp_plan: filter path %d not built", o.filter_path);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    if (o.filter_path == FBP_PATH_TOEPLITZ_TC &&
+        (o.dtype != FBP_F32 || o.q_storage != FBP_F32)) {
+        set_error("fbp_plan: the tensor-core filter writes FP32 pairs of FP32 plans");
         return FBP_ERR_UNSUPPORTED;
     }
     // FFT length: any power of two >= 2*n_det - 1 gives the linear convolution.
@@ -396,6 +462,11 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         if (e == cudaSuccess)
             e = cudaMemcpy(p->d_fft_h, hs.data(), sizeof(float) * (size_t)N, cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && p->filter_path == FBP_PATH_TOEPLITZ_TC) {
+        p->tc = new TcTables();
+        std::memset(p->tc, 0, sizeof(TcTables));
+        e = make_tc_tables(*p, taps, p->tc) ? cudaSuccess : cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -455,6 +526,9 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
                                      static_cast<double *>(filtered), stream);
     else if (p->filter_path == FBP_PATH_FFT)
         e = launch_filter_fft(*p, static_cast<const float *>(sino), ld_sino, filtered, stream);
+    else if (p->filter_path == FBP_PATH_TOEPLITZ_TC)
+        e = launch_filter_tc(*p, static_cast<const float *>(sino), ld_sino,
+                             static_cast<float *>(filtered), stream);
     else
         e = launch_filter_direct(*p, static_cast<const float *>(sino), ld_sino, filtered, stream);
     return e == cudaSuccess ? FBP_OK : cuda_fail(e, "fbp_filter");

@@ -13,6 +13,7 @@
 
 #include "backproject.cuh"
 #include "fbp_internal.h"
+#include "filter_tc.cuh"
 
 namespace fbp {
 BpSlice slice_desc(const Plan &p, float *image);
@@ -59,11 +60,14 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
 {
     for (int i = 0; i < n && (parts & FBP_BATCH_FILTER); ++i) {
         const Plan &p = *plans[i];
-        cudaError_t e = (p.filter_path == FBP_PATH_FFT)
-                            ? launch_filter_fft(p, static_cast<const float *>(io[i].sino),
-                                                io[i].ld_sino, io[i].workspace, s)
-                            : launch_filter_direct(p, static_cast<const float *>(io[i].sino),
-                                                   io[i].ld_sino, io[i].workspace, s);
+        const float *sino = static_cast<const float *>(io[i].sino);
+        cudaError_t e;
+        if (p.filter_path == FBP_PATH_FFT)
+            e = launch_filter_fft(p, sino, io[i].ld_sino, io[i].workspace, s);
+        else if (p.filter_path == FBP_PATH_TOEPLITZ_TC)
+            e = launch_filter_tc(p, sino, io[i].ld_sino, static_cast<float *>(io[i].workspace), s);
+        else
+            e = launch_filter_direct(p, sino, io[i].ld_sino, io[i].workspace, s);
         if (e != cudaSuccess) return e;
     }
     if (!(parts & FBP_BATCH_BACKPROJECT)) return cudaSuccess;

@@ -14,6 +14,8 @@ namespace fbp {
 constexpr int kBpChunk = 16;      // angles per shared-memory stage of the backprojection
 constexpr int kMaxFftLen = 8192;  // FP32 FFT route: two N-point complex buffers in shared memory
 
+struct TcTables;  // tensor-core filter tables (filter_tc.cuh)
+
 struct Plan {
     int n;      // image side
     int A;      // angles
@@ -41,6 +43,7 @@ struct Plan {
     float2 *d_fft_tw;   // FFT route: exp(-2 pi i t / N), t < N
     float *d_fft_h;     // FFT route: DFT_N of the circular taps, times 1/N (real, even)
     int *d_status;      // device status word (0 = ok)
+    TcTables *tc;       // Toeplitz route: T_hi / T_lo and their TMA maps
 };
 
 // Element size of the filtered sinogram.

@@ -1,0 +1,321 @@
+// Ramp filter Q = P * H (the convolution stated after Eq. 2) as a dense
+// Toeplitz contraction on the 5th-generation tensor cores:
+//     Q[i][n] = sum_k P[i][k] T[n][k],   T[n][k] = tau h(n - k),
+// an (A x D) . (D x D)^T GEMM.  FP32 accuracy from TF32 units by the 3xTF32
+// split: x = x_hi + x_lo with x_hi = tf32(x) (round to nearest) and
+// x_lo = x - x_hi, and P T ~= P_hi T_hi + P_hi T_lo + P_lo T_hi, each product
+// accumulated in FP32 in tensor memory.  T_hi and T_lo are plan tables.
+//
+// One CTA per 128 x 128 output tile (rows m0.., output bins n0 = 126 t - 1 ..):
+//   warp 0 (lane 0) issues tcgen05.mma, K-chunk after K-chunk (32 columns);
+//   warp 1 (lane 0) brings T_hi/T_lo tiles in with 2D TMA (128-byte swizzle);
+//   warps 2..5 load the sinogram rows with coalesced loads, split them into
+//   tf32 hi/lo and store both in the same swizzled layout, then run the
+//   epilogue: tcgen05.ld of the accumulator, (mid, slope) pairs of
+//   consecutive bins, stores to the filtered rows.
+// Tiles step by 126 output pairs and overlap by two columns so every pair's
+// two bins sit in one tile; the row n0 = -1 of the first tile is out of bounds
+// for TMA and arrives as zeros, which is Q[-1] = 0.  A NSTAGE-deep mbarrier
+// ring (full: data landed, empty: MMAs done reading) keeps loads and MMAs
+// overlapped.  The tensor core's FP32 accumulation loses low bits at every
+// accumulate step, so K-chunks go round-robin to four accumulators (all 512
+// TMEM columns) that the epilogue adds in FP32 registers: each sees a quarter
+// of the steps.  Every wait is bounded; on a timeout the CTA records the
+// status, releases its tensor memory and exits.
+#include "fbp_internal.h"
+#include "filter_tc.cuh"
+#include "ptx.cuh"
+
+namespace fbp {
+namespace {
+
+constexpr int kBM = 128;      // output rows per tile (TMEM lanes)
+constexpr int kBN = 128;      // output bins per tile (TMEM columns)
+constexpr int kStep = 126;    // output pairs per tile
+constexpr int kBK = 32;       // fp32 elements per 128-byte swizzle row
+constexpr int kStages = 3;
+constexpr int kAcc = 4;       // accumulators (TMEM column blocks), K-chunks round-robin
+constexpr int kTile = kBM * kBK * 4;          // 16 KB per operand tile
+constexpr int kStageBytes = 4 * kTile;        // A_hi, A_lo, B_hi, B_lo
+constexpr int kThreads = 192;
+
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// 8-row x 128-byte atoms stacked 1024 bytes apart along M/N.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 1024 B
+    d |= (uint64_t)1 << 46;                            // descriptor version (sm_100)
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
+// M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cta(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcArgs {
+    const float *sino;
+    float *q;  // filtered pairs [A][pitch]
+    int ld;
+    int A;
+    int D;
+    int pitch;
+    int nk;  // K chunks
+    int *status;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    filter_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant__ CUtensorMap t_lo,
+                     const TcArgs args)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t s0 = smem_addr(smem);
+    const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-byte aligned: swizzle atoms
+    unsigned char *bp = smem + (base - s0);
+    const uint32_t bar_full_a = base + kStages * kStageBytes;      // [kStages], 128 arrivals
+    const uint32_t bar_full_b = bar_full_a + 8 * kStages;          // [kStages], TMA bytes
+    const uint32_t bar_empty = bar_full_b + 8 * kStages;           // [kStages], MMA commit
+    const uint32_t bar_acc = bar_empty + 8 * kStages;              // accumulator ready
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bp + kStages * kStageBytes + 8 * (3 * kStages + 1));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int n_tile = blockIdx.x;
+    const int m0 = blockIdx.y * kBM;
+    const int n0 = n_tile * kStep - 1;  // first output bin of the tile
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(bar_full_a + 8 * s, 128);
+            mbar_init(bar_full_b + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_acc, 1);
+        *abort_flag = 0;
+        fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tmem_slot)),
+                     "r"(kAcc * kBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto fail = [&]() {
+        *reinterpret_cast<volatile int *>(args.status) = FBP_ERR_TIMEOUT;
+        *abort_flag = 1;
+    };
+
+    if (warp == 0) {
+        // -------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            for (int kc = 0; kc < args.nk && !*abort_flag; ++kc) {
+                const int s = kc % kStages;
+                const uint32_t ph = (uint32_t)(kc / kStages) & 1u;
+                if (!mbar_wait_bounded(bar_full_a + 8 * s, ph) ||
+                    !mbar_wait_bounded(bar_full_b + 8 * s, ph)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = base + s * kStageBytes;
+                const uint32_t a_hi = st, a_lo = st + kTile, b_hi = st + 2 * kTile,
+                               b_lo = st + 3 * kTile;
+                const uint32_t d = tmem + (uint32_t)((kc % kAcc) * kBN);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 8; ++kk) {  // K = 8 tf32 = 32 bytes per MMA
+                    const uint32_t off = 32u * kk;
+                    const uint32_t acc = (kc >= kAcc || kk > 0) ? 1u : 0u;
+                    mma_tf32(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), acc);
+                    mma_tf32(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
+                    mma_tf32(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), 1u);
+                }
+                mma_commit(bar_empty + 8 * s);  // stage s free once these MMAs have read it
+            }
+            mma_commit(bar_acc);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // -------------------------------------------------------- T tiles by TMA
+        if (lane == 0) {
+            for (int kc = 0; kc < args.nk && !*abort_flag; ++kc) {
+                const int s = kc % kStages;
+                const uint32_t use = (uint32_t)(kc / kStages);
+                if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u)) {
+                    fail();
+                    break;
+                }
+                const uint32_t st = base + s * kStageBytes;
+                mbar_arrive_expect_tx(bar_full_b + 8 * s, 2 * kTile);
+                tma_load_2d(st + 2 * kTile, &t_hi, kc * kBK, n0, bar_full_b + 8 * s);
+                tma_load_2d(st + 3 * kTile, &t_lo, kc * kBK, n0, bar_full_b + 8 * s);
+            }
+        }
+        __syncwarp();
+    } else {
+        // -------------------------------------------------------- A split, then epilogue
+        const int cw = warp - 2;  // 0..3: rows 32 cw .. 32 cw + 31 of the tile
+        for (int kc = 0; kc < args.nk; ++kc) {
+            const int s = kc % kStages;
+            const uint32_t use = (uint32_t)(kc / kStages);
+            if (*abort_flag) break;
+            if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u)) {
+                fail();
+                break;
+            }
+            unsigned char *a_hi = bp + s * kStageBytes;
+            unsigned char *a_lo = a_hi + kTile;
+            const int k = kc * kBK + lane;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                const int r = cw * 32 + i;
+                const int m = m0 + r;
+                const float x = (m < args.A && k < args.D) ? __ldg(&args.sino[(size_t)m * args.ld + k]) : 0.0f;
+                const uint32_t hi = tf32_rna(x);
+                const float lo = x - __uint_as_float(hi);
+                // 128-byte swizzle: 16-byte chunk (lane / 4) XOR (row mod 8)
+                const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 +
+                                                ((((lane >> 2) ^ (r & 7)) << 4) | ((lane & 3) << 2)));
+                *reinterpret_cast<uint32_t *>(a_hi + off) = hi;
+                *reinterpret_cast<float *>(a_lo + off) = lo;
+            }
+            fence_proxy_async_smem();  // generic-proxy stores -> tensor-core reads
+            mbar_arrive_cta(bar_full_a + 8 * s);
+        }
+        // epilogue: this warp owns TMEM lanes 32 (warp % 4) .. +31 = tile rows
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;
+        const int m = m0 + r;
+        const bool ok = mbar_wait_bounded(bar_acc, 0);
+        if (!ok) fail();
+        tc_fence_after();
+        if (ok && !*abort_flag) {
+            // column j holds Q[n0 + j]; pair p = 126 t + j takes columns j, j + 1
+            float v[kBN / 32][32];
+            const int used = args.nk < kAcc ? args.nk : kAcc;  // accumulators written
+#pragma unroll
+            for (int c = 0; c < kBN / 32; ++c) {
+                const uint32_t lane_col = ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32);
+                tmem_ld32(tmem + lane_col, v[c]);
+                for (int a = 1; a < used; ++a) {
+                    float w[32];
+                    tmem_ld32(tmem + lane_col + (uint32_t)(a * kBN), w);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[c][j] += w[j];
+                }
+            }
+            if (m < args.A) {
+                float *row = args.q + (size_t)m * args.pitch;
+                const int p0 = n_tile * kStep;  // even: float4 = two pairs, 16-byte aligned
+                const int npairs = args.pitch / 2;
+#pragma unroll
+                for (int j = 0; j < kStep; j += 2) {
+                    if (p0 + j < npairs) {
+                        const float a0 = v[j / 32][j % 32];
+                        const float a1 = v[(j + 1) / 32][(j + 1) % 32];
+                        const float a2 = v[(j + 2) / 32][(j + 2) % 32];
+                        *reinterpret_cast<float4 *>(row + 2 * (p0 + j)) =
+                            make_float4((a0 + a1) * 0.5f, a1 - a0, (a1 + a2) * 0.5f, a2 - a1);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kAcc * kBN)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t filter_tc_smem_bytes() { return (size_t)kStages * kStageBytes + 8 * (3 * kStages + 1) + 16 + 1024; }
+
+cudaError_t launch_filter_tc(const Plan &p, const float *sino, int ld, float *q, cudaStream_t s)
+{
+    TcArgs a;
+    a.sino = sino;
+    a.q = q;
+    a.ld = ld;
+    a.A = p.A;
+    a.D = p.D;
+    a.pitch = p.pitch;
+    a.nk = (p.D + kBK - 1) / kBK;
+    a.status = p.d_status;
+    const size_t smem = filter_tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(filter_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.pitch / 2 + kStep - 1) / kStep, (p.A + kBM - 1) / kBM);
+    filter_tc_kernel<<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);
+    return cudaGetLastError();
+}
+
+}  // namespace fbp

@@ -91,12 +91,12 @@ def test_results_in_the_mix_equal_alone(fbp):
 
 
 def test_small_budget_stalls_admission_but_completes(fbp):
-    """A budget that holds about two requests: the rest wait for memory, in order."""
+    """A budget that holds one of the largest requests: the rest wait for memory, in order."""
     reqs = _stream(12, seed=62)
     bufs = [_host(s) for _, s in reqs]
     biggest = max(4 * (s.n_angles * s.n_det + s.n_angles * (2 * s.n_det + 16) + s.n_pix ** 2)
                   for _, s in reqs)
-    server = fbp.Server(hbm_budget_bytes=2 * biggest + (1 << 20), max_wave=4, n_streams=2)
+    server = fbp.Server(hbm_budget_bytes=max(biggest + 4096, 1 << 20), max_wave=4, n_streams=2)
     ids = [server.submit(s, img, spec.n_pix) for (_, spec), (s, img) in zip(reqs, bufs)]
     server.drain(120.0)
     st = server.stats()
