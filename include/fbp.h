@@ -282,6 +282,28 @@ fbp_status fbp_server_get_stats(fbp_server_t server, fbp_server_stats *out);
 /* Stop the worker, wait for the streams, release plans and the arena. NULL is a no-op. */
 fbp_status fbp_server_destroy(fbp_server_t server);
 
+/* ------------------------------------------------------------------ tuning
+ * Choice of the filter route (FFT, tensor-core Toeplitz, direct) and of the
+ * backprojection launch shape (pixel tile, angles per shared-memory stage) for
+ * one geometry, by timing every candidate on the device over `batch` slices.
+ * Cached in memory per (GPU model, geometry, base options, batch); when the
+ * environment variable FBP_TUNE_CACHE names a file, results are appended to it
+ * and read back by later processes.  Plans made with the returned options give
+ * the same bits alone, in batches and in the server. */
+typedef struct {
+    fbp_options options;   /* base options with filter_path, fft_len, tile_x, tile_y,
+                              angle_chunk filled in */
+    double filter_ms;      /* per slice, best route */
+    double backproject_ms; /* per slice, best shape */
+    int from_cache;
+} fbp_tuning;
+
+/* Tune the geometry (allocates test buffers for `batch` (1..64) slices while it
+ * runs; synchronises the device).  base may be NULL (defaults); FP32 only. */
+fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
+                        fbp_filter_type filter, const fbp_options *base, int batch,
+                        fbp_tuning *out);
+
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

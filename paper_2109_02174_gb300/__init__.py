@@ -64,6 +64,11 @@ class fbp_options(ctypes.Structure):
                  "tile_x", "tile_y", "angle_chunk")]
 
 
+class fbp_tuning(ctypes.Structure):
+    _fields_ = [("options", fbp_options), ("filter_ms", ctypes.c_double),
+                ("backproject_ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -89,6 +94,8 @@ _SIGS = {
                               ctypes.POINTER(fbp_batch_io), _I, _P],
     "fbp_batch_launch": [_P, _P],
     "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
+    "fbp_autotune": [_I, _I, _I, ctypes.c_double, _I, ctypes.POINTER(fbp_options), _I,
+                     ctypes.POINTER(fbp_tuning)],
     "fbp_server_create": [ctypes.POINTER(_P), ctypes.c_size_t, _I, _I],
     "fbp_server_warm": [_P, _I, _I, _I, ctypes.c_double, _I],
     "fbp_server_submit": [_P, ctypes.POINTER(fbp_request), ctypes.POINTER(ctypes.c_longlong)],
@@ -240,15 +247,35 @@ def fbp_batch_destroy(batch: int):
     _check(load_library().fbp_batch_destroy(batch))
 
 
+def fbp_autotune(n_pix, n_angles, n_det, det_spacing=1.0, filter=FBP_FILTER_RAM_LAK,
+                 base: fbp_options | None = None, batch: int = 8) -> dict:
+    """Tuned options for a geometry (see fbp.h): a dict of option fields plus
+    filter_ms / backproject_ms (per slice) and from_cache."""
+    t = fbp_tuning()
+    _check(load_library().fbp_autotune(int(n_pix), int(n_angles), int(n_det), float(det_spacing),
+                                       int(filter), ctypes.byref(base) if base else None,
+                                       int(batch), ctypes.byref(t)))
+    d = {name: getattr(t.options, name) for name, _ in fbp_options._fields_}
+    d.update(filter_ms=t.filter_ms, backproject_ms=t.backproject_ms, from_cache=t.from_cache)
+    return d
+
+
 # ------------------------------------------------------------ tensor wrapper
 class Plan:
     """A reconstruction plan bound to torch tensors on the current CUDA device."""
 
     def __init__(self, n_pix: int, n_angles: int, n_det: int, angles=None,
-                 det_spacing: float = 1.0, filter: int = FBP_FILTER_RAM_LAK, **options):
+                 det_spacing: float = 1.0, filter: int = FBP_FILTER_RAM_LAK,
+                 autotune: bool = False, batch_hint: int = 8, **options):
         opt = fbp_options_default()
         for k, v in options.items():
             setattr(opt, k, int(v))
+        self.tuning = None
+        if autotune:
+            self.tuning = fbp_autotune(n_pix, n_angles, n_det, det_spacing, filter, opt,
+                                       batch_hint)
+            for k in ("filter_path", "fft_len", "tile_x", "tile_y", "angle_chunk"):
+                setattr(opt, k, int(self.tuning[k]))
         self.n_pix, self.n_angles, self.n_det = int(n_pix), int(n_angles), int(n_det)
         self.det_spacing = float(det_spacing)
         self.filter_type = int(filter)

@@ -134,6 +134,7 @@ BpConfig bp_config(const Plan &p)
     BpConfig c;
     c.wx = p.bp_wx;
     c.wy = p.bp_wy;
+    c.chunk = p.bp_chunk;
     c.half_pairs = p.q_storage == FBP_F16;
     c.kahan = p.accumulate == FBP_ACC_KAHAN;
     return c;
@@ -416,6 +417,12 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     p->bp_wx = shapes[pick][0];
     p->bp_wy = shapes[pick][1];
     p->bp_wp = window_pairs(trig, 8 * p->bp_wx, 32 * p->bp_wy, align);
+    if (o.angle_chunk != 0 && o.angle_chunk != 8 && o.angle_chunk != 16 && o.angle_chunk != 32) {
+        delete p;
+        set_error("fbp_plan: angle_chunk %d is not 8, 16 or 32", o.angle_chunk);
+        return FBP_ERR_INVALID_ARG;
+    }
+    p->bp_chunk = o.angle_chunk ? o.angle_chunk : 16;
 
     std::vector<double> taps;
     make_taps((int)filter, n_det, det_spacing, taps);

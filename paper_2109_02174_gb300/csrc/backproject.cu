@@ -104,7 +104,7 @@ __device__ __forceinline__ int2 item_of(const BpLaunch<MAXS> &P, int item)
     return make_int2(lo, item - (lo > 0 ? P.tile_end[lo - 1] : 0));
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int CH, int MAXS>
 __global__ void __launch_bounds__(32 * (WX * WY + 1))
     bp_persistent_kernel(const __grid_constant__ BpLaunch<MAXS> P)
 {
@@ -112,10 +112,10 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
     constexpr int TX = 8 * WX;             // tile width  (warp footprint 8 wide)
     constexpr int TY = 32 * WY;            // tile height (warp covers 32 rows)
     constexpr int PPT = 8;                 // pixels per consumer thread (rows ly0 + 4j)
-    constexpr int CH = kBpChunk;
-    constexpr int NSTAGE = kBpStages;
+    constexpr int NSTAGE = bp_stages(CH);
     using TR = PairTraits<PairT>;
     using L_t = Layout<NSTAGE, CH>;
+    static_assert(CH <= 32, "one producer lane per angle of a chunk");
 
     extern __shared__ __align__(128) unsigned char smem[];
     const L_t L = L_t::make(P.wp_max, TR::kBytes);
@@ -280,12 +280,12 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
     }
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int CH, int MAXS>
 cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
 {
-    using L_t = Layout<kBpStages, kBpChunk>;
+    using L_t = Layout<bp_stages(CH), CH>;
     const L_t L = L_t::make(P.wp_max, PairTraits<PairT>::kBytes);
-    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, MAXS>;
+    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, CH, MAXS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          L.total);
     if (e != cudaSuccess) return e;
@@ -304,28 +304,30 @@ cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
+cudaError_t by_chunk(const BpLaunch<MAXS> &P, int chunk, int grid_limit, cudaStream_t s)
+{
+    if (chunk == 8) return launch_one<PairT, KAHAN, WX, WY, 8, MAXS>(P, grid_limit, s);
+    if (chunk == 32) return launch_one<PairT, KAHAN, WX, WY, 32, MAXS>(P, grid_limit, s);
+    if (chunk == 16) return launch_one<PairT, KAHAN, WX, WY, 16, MAXS>(P, grid_limit, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int WX, int WY, int MAXS>
+cudaError_t by_variant(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit, cudaStream_t s)
+{
+    if (!c.half_pairs && !c.kahan) return by_chunk<float, false, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
+    if (!c.half_pairs && c.kahan) return by_chunk<float, true, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
+    if (c.half_pairs && !c.kahan) return by_chunk<__half, false, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
+    return by_chunk<__half, true, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
+}
+
 template <int MAXS>
 cudaError_t dispatch(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit, cudaStream_t s)
 {
-    const bool h = c.half_pairs, k = c.kahan;
-    if (c.wx == 4 && c.wy == 2) {
-        if (!h && !k) return launch_one<float, false, 4, 2, MAXS>(P, grid_limit, s);
-        if (!h && k) return launch_one<float, true, 4, 2, MAXS>(P, grid_limit, s);
-        if (h && !k) return launch_one<__half, false, 4, 2, MAXS>(P, grid_limit, s);
-        return launch_one<__half, true, 4, 2, MAXS>(P, grid_limit, s);
-    }
-    if (c.wx == 4 && c.wy == 1) {
-        if (!h && !k) return launch_one<float, false, 4, 1, MAXS>(P, grid_limit, s);
-        if (!h && k) return launch_one<float, true, 4, 1, MAXS>(P, grid_limit, s);
-        if (h && !k) return launch_one<__half, false, 4, 1, MAXS>(P, grid_limit, s);
-        return launch_one<__half, true, 4, 1, MAXS>(P, grid_limit, s);
-    }
-    if (c.wx == 1 && c.wy == 1) {
-        if (!h && !k) return launch_one<float, false, 1, 1, MAXS>(P, grid_limit, s);
-        if (!h && k) return launch_one<float, true, 1, 1, MAXS>(P, grid_limit, s);
-        if (h && !k) return launch_one<__half, false, 1, 1, MAXS>(P, grid_limit, s);
-        return launch_one<__half, true, 1, 1, MAXS>(P, grid_limit, s);
-    }
+    if (c.wx == 4 && c.wy == 2) return by_variant<4, 2, MAXS>(P, c, grid_limit, s);
+    if (c.wx == 4 && c.wy == 1) return by_variant<4, 1, MAXS>(P, c, grid_limit, s);
+    if (c.wx == 1 && c.wy == 1) return by_variant<1, 1, MAXS>(P, c, grid_limit, s);
     return cudaErrorInvalidValue;
 }
 

@@ -7,7 +7,8 @@
 
 namespace fbp {
 
-constexpr int kBpStages = 4;      // shared-memory ring depth (chunks of kBpChunk angles)
+// Shared-memory ring: stages of `chunk` angles each, 64 angles in flight.
+__host__ __device__ constexpr int bp_stages(int chunk) { return chunk >= 32 ? 2 : 64 / chunk; }
 constexpr int kBpMaxSlices = 64;  // slices per batched launch (tensor maps in the parameters)
 
 // One slice of a launch.
@@ -44,6 +45,7 @@ struct BpLaunch {
 struct BpConfig {
     int wx;
     int wy;
+    int chunk;        // angles per stage: 8, 16 or 32
     bool half_pairs;  // FP16-stored (mid, slope) pairs
     bool kahan;       // Kahan-compensated sum over angles
 };

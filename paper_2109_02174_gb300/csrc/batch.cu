@@ -58,17 +58,27 @@ namespace fbp {
 cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
                          int *status, cudaStream_t s)
 {
-    for (int i = 0; i < n && (parts & FBP_BATCH_FILTER); ++i) {
-        const Plan &p = *plans[i];
-        const float *sino = static_cast<const float *>(io[i].sino);
-        cudaError_t e;
-        if (p.filter_path == FBP_PATH_FFT)
-            e = launch_filter_fft(p, sino, io[i].ld_sino, io[i].workspace, s);
-        else if (p.filter_path == FBP_PATH_TOEPLITZ_TC)
-            e = launch_filter_tc(p, sino, io[i].ld_sino, static_cast<float *>(io[i].workspace), s);
-        else
-            e = launch_filter_direct(p, sino, io[i].ld_sino, io[i].workspace, s);
+    if (parts & FBP_BATCH_FILTER) {
+        // FFT-route slices: one launch over all their row pairs
+        std::vector<const float *> sinos((size_t)n);
+        std::vector<int> lds((size_t)n);
+        std::vector<void *> qs((size_t)n);
+        for (int i = 0; i < n; ++i) {
+            sinos[(size_t)i] = static_cast<const float *>(io[i].sino);
+            lds[(size_t)i] = io[i].ld_sino;
+            qs[(size_t)i] = io[i].workspace;
+        }
+        cudaError_t e = launch_filter_fft_many(plans, sinos.data(), lds.data(), qs.data(), n, s);
         if (e != cudaSuccess) return e;
+        for (int i = 0; i < n; ++i) {
+            const Plan &p = *plans[i];
+            if (p.filter_path == FBP_PATH_FFT) continue;
+            e = (p.filter_path == FBP_PATH_TOEPLITZ_TC)
+                    ? launch_filter_tc(p, sinos[(size_t)i], lds[(size_t)i],
+                                       static_cast<float *>(qs[(size_t)i]), s)
+                    : launch_filter_direct(p, sinos[(size_t)i], lds[(size_t)i], qs[(size_t)i], s);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (!(parts & FBP_BATCH_BACKPROJECT)) return cudaSuccess;
     std::map<std::tuple<int, int, int, int>, std::vector<int>> by_cfg;

@@ -11,8 +11,8 @@
 
 namespace fbp {
 
-constexpr int kBpChunk = 16;      // angles per shared-memory stage of the backprojection
 constexpr int kMaxFftLen = 8192;  // FP32 FFT route: two N-point complex buffers in shared memory
+constexpr int kFftMaxSlices = 64; // slices per batched FFT launch
 
 struct TcTables;  // tensor-core filter tables (filter_tc.cuh)
 
@@ -34,6 +34,7 @@ struct Plan {
     int bp_wx;
     int bp_wy;
     int bp_wp;
+    int bp_chunk;  // angles per shared-memory stage (8, 16, 32)
     float scale32;   // pi / A
     double scale64;  // pi / A
     // Device tables owned by the plan.
@@ -63,6 +64,10 @@ bool encode_pairs_map(const Plan &p, const void *q, CUtensorMap *out);
 cudaError_t launch_filter_direct(const Plan &p, const float *sino, int ld, void *q,
                                  cudaStream_t s);
 cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q, cudaStream_t s);
+// The FFT-route slices among plans[0..n) in as few launches as possible
+// (other slices are skipped).
+cudaError_t launch_filter_fft_many(const Plan *const *plans, const float *const *sinos,
+                                   const int *lds, void *const *qs, int n, cudaStream_t s);
 size_t filter_fft_smem_bytes(int N);
 size_t filter_direct_smem_bytes(int D);
 

@@ -11,6 +11,8 @@
 // autosort FFT (one radix-2 pass first when log2 N is odd) ping-ponging
 // between two shared-memory buffers; twiddles exp(-2 pi i t / N) come from a
 // plan table computed in FP64.  The 1/N of the inverse is folded into H.
+// One launch can cover the row pairs of many slices (their plans may differ),
+// so a batch fills the GPU instead of running slice after slice.
 #include "fbp_internal.h"
 #include "pairs.cuh"
 
@@ -90,19 +92,48 @@ __device__ float2 *fft(float2 *x, float2 *y, const float2 *__restrict__ tw, int 
     return x;
 }
 
-template <typename OutT>
-__global__ void __launch_bounds__(256)
-    filter_fft_kernel(const float *__restrict__ sino, int ld, const float2 *__restrict__ tw,
-                      const float *__restrict__ hspec, OutT *__restrict__ q, int A, int D,
-                      int pitch, int N, int log2n)
+// One slice's part of a launch; pair_end is the inclusive prefix sum of the
+// slices' row-pair counts, so CTA b works on the slice s with
+// pair_end[s-1] <= b < pair_end[s].
+struct FftSlice {
+    const float *sino;
+    void *q;
+    const float2 *tw;
+    const float *h;
+    int ld;
+    int pitch;
+    int A;
+    int D;
+    int N;
+    int log2n;
+    int pair_end;
+    int pad_;
+};
+
+template <int MAXS>
+struct FftLaunch {
+    FftSlice s[MAXS];
+    int n;
+};
+
+template <typename OutT, int MAXS>
+__global__ void __launch_bounds__(256) filter_fft_kernel(const __grid_constant__ FftLaunch<MAXS> L)
 {
     extern __shared__ float2 buf[];
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)blockIdx.x < L.s[mid].pair_end) hi = mid; else lo = mid + 1;
+    }
+    const FftSlice &S = L.s[lo];
+    const int pair = (int)blockIdx.x - (lo > 0 ? L.s[lo - 1].pair_end : 0);
+    const int N = S.N, D = S.D;
     float2 *x = buf;
     float2 *y = buf + N;
-    const int i0 = 2 * blockIdx.x;
-    const bool two = i0 + 1 < A;
-    const float *p0 = sino + (size_t)i0 * ld;
-    const float *p1 = sino + (size_t)(two ? i0 + 1 : i0) * ld;
+    const int i0 = 2 * pair;
+    const bool two = i0 + 1 < S.A;
+    const float *p0 = S.sino + (size_t)i0 * S.ld;
+    const float *p1 = S.sino + (size_t)(two ? i0 + 1 : i0) * S.ld;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         float2 v = make_float2(0.0f, 0.0f);
         if (j < D) {
@@ -112,18 +143,18 @@ __global__ void __launch_bounds__(256)
         x[j] = v;
     }
     __syncthreads();
-    float2 *z = fft(x, y, tw, N, log2n, false);
+    float2 *z = fft(x, y, S.tw, N, S.log2n, false);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const float h = __ldg(&hspec[j]);
-        z[j] = make_float2(z[j].x * h, z[j].y * h);
+        const float hv = __ldg(&S.h[j]);
+        z[j] = make_float2(z[j].x * hv, z[j].y * hv);
     }
     __syncthreads();
     float2 *other = (z == x) ? y : x;
-    z = fft(z, other, tw, N, log2n, true);
+    z = fft(z, other, S.tw, N, S.log2n, true);
     // z[k] = (Q_i0[k], Q_i0+1[k]) for k < n_det; write (mid, slope) pairs.
-    OutT *r0 = q + (size_t)i0 * pitch;
-    OutT *r1 = q + (size_t)(i0 + 1) * pitch;
-    for (int p = threadIdx.x; p < pitch / 2; p += blockDim.x) {
+    OutT *r0 = static_cast<OutT *>(S.q) + (size_t)i0 * S.pitch;
+    OutT *r1 = static_cast<OutT *>(S.q) + (size_t)(i0 + 1) * S.pitch;
+    for (int p = threadIdx.x; p < S.pitch / 2; p += blockDim.x) {
         float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
         if (p <= D) {
             if (p >= 1) a = z[p - 1];
@@ -134,30 +165,84 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <typename OutT, int MAXS>
+cudaError_t launch_set(const FftLaunch<MAXS> &L, int total, int nmax, cudaStream_t s)
+{
+    const size_t smem = sizeof(float2) * (size_t)(2 * nmax);
+    cudaError_t e = cudaFuncSetAttribute(filter_fft_kernel<OutT, MAXS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    filter_fft_kernel<OutT, MAXS><<<total, 256, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+FftSlice fft_slice(const Plan &p, const float *sino, int ld, void *q)
+{
+    FftSlice f;
+    f.sino = sino;
+    f.q = q;
+    f.tw = p.d_fft_tw;
+    f.h = p.d_fft_h;
+    f.ld = ld;
+    f.pitch = p.pitch;
+    f.A = p.A;
+    f.D = p.D;
+    f.N = p.fft_len;
+    int log2n = 0;
+    while ((1 << log2n) < p.fft_len) ++log2n;
+    f.log2n = log2n;
+    f.pair_end = 0;
+    f.pad_ = 0;
+    return f;
+}
+
 }  // namespace
 
 size_t filter_fft_smem_bytes(int N) { return sizeof(float2) * (size_t)(2 * N); }
 
-namespace {
-template <typename OutT>
-cudaError_t launch(const Plan &p, const float *sino, int ld, OutT *q, cudaStream_t s)
-{
-    const size_t smem = filter_fft_smem_bytes(p.fft_len);
-    cudaError_t e = cudaFuncSetAttribute(filter_fft_kernel<OutT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int log2n = 0;
-    while ((1 << log2n) < p.fft_len) ++log2n;
-    filter_fft_kernel<OutT><<<(p.A + 1) / 2, 256, smem, s>>>(sino, ld, p.d_fft_tw, p.d_fft_h, q,
-                                                            p.A, p.D, p.pitch, p.fft_len, log2n);
-    return cudaGetLastError();
-}
-}  // namespace
-
 cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q, cudaStream_t s)
 {
-    if (p.q_storage == FBP_F16) return launch(p, sino, ld, static_cast<__half *>(q), s);
-    return launch(p, sino, ld, static_cast<float *>(q), s);
+    FftLaunch<1> L;
+    L.s[0] = fft_slice(p, sino, ld, q);
+    L.s[0].pair_end = (p.A + 1) / 2;
+    L.n = 1;
+    if (p.q_storage == FBP_F16) return launch_set<__half, 1>(L, L.s[0].pair_end, p.fft_len, s);
+    return launch_set<float, 1>(L, L.s[0].pair_end, p.fft_len, s);
+}
+
+cudaError_t launch_filter_fft_many(const Plan *const *plans, const float *const *sinos,
+                                   const int *lds, void *const *qs, int n, cudaStream_t s)
+{
+    // one launch per (storage type, up to kFftMaxSlices slices)
+    for (int half = 0; half < 2; ++half) {
+        FftLaunch<kFftMaxSlices> L;
+        int cnt = 0, total = 0, nmax = 16;
+        auto flush = [&]() -> cudaError_t {
+            if (cnt == 0) return cudaSuccess;
+            L.n = cnt;
+            cudaError_t e = half ? launch_set<__half, kFftMaxSlices>(L, total, nmax, s)
+                                 : launch_set<float, kFftMaxSlices>(L, total, nmax, s);
+            cnt = 0;
+            total = 0;
+            nmax = 16;
+            return e;
+        };
+        for (int i = 0; i < n; ++i) {
+            const Plan &p = *plans[i];
+            if (p.filter_path != FBP_PATH_FFT || (p.q_storage == FBP_F16) != (half == 1)) continue;
+            L.s[cnt] = fft_slice(p, sinos[i], lds[i], qs[i]);
+            total += (p.A + 1) / 2;
+            L.s[cnt].pair_end = total;
+            nmax = p.fft_len > nmax ? p.fft_len : nmax;
+            if (++cnt == kFftMaxSlices) {
+                cudaError_t e = flush();
+                if (e != cudaSuccess) return e;
+            }
+        }
+        cudaError_t e = flush();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace fbp

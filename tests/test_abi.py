@@ -64,3 +64,10 @@ def test_plan_argument_errors_are_host_side(lib):
         st = lib.fbp_plan(ctypes.byref(h), n, a, d, None, tau, flt, None)
         assert st == fbp.FBP_ERR_INVALID_ARG, args
         assert h.value is None
+
+
+def test_autotune_argument_errors_need_no_gpu(lib):
+    import paper_2109_02174_gb300 as fbp
+    t = fbp.fbp_tuning()
+    assert lib.fbp_autotune(64, 90, 92, 1.0, 0, None, 0, ctypes.byref(t)) == fbp.FBP_ERR_INVALID_ARG
+    assert lib.fbp_autotune(64, 90, 92, 1.0, 0, None, 4, None) == fbp.FBP_ERR_INVALID_ARG

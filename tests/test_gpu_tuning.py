@@ -1,0 +1,86 @@
+"""GPU: the autotuner picks a valid filter route and backprojection shape per
+geometry, caches it (in memory and in the FBP_TUNE_CACHE file), and plans made
+from its choice meet the parity bars; the angle chunk never changes the bits."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_02174_gb300 import build
+    build.build()
+    import paper_2109_02174_gb300 as m
+    return m
+
+
+def test_autotune_choice_is_valid_and_cached(fbp):
+    n, A = 128, 180
+    D = synthetic.det_for(n)
+    t1 = fbp.fbp_autotune(n, A, D, batch=4)
+    assert (t1["tile_x"], t1["tile_y"]) in {(32, 64), (32, 32), (8, 32)}
+    assert t1["angle_chunk"] in (8, 16, 32)
+    assert t1["filter_path"] in (fbp.FBP_PATH_TOEPLITZ_TC, fbp.FBP_PATH_FFT, fbp.FBP_PATH_DIRECT)
+    assert t1["filter_ms"] > 0 and t1["backproject_ms"] > 0
+    t2 = fbp.fbp_autotune(n, A, D, batch=4)
+    assert t2["from_cache"] == 1
+    assert {k: t2[k] for k in ("tile_x", "tile_y", "angle_chunk", "filter_path")} == \
+        {k: t1[k] for k in ("tile_x", "tile_y", "angle_chunk", "filter_path")}
+
+
+def test_tuned_plan_meets_bars_and_batches_bitwise(fbp):
+    import torch
+    spec = synthetic.SliceSpec(160, 200, synthetic.det_for(160), 6, seed=71, filter=1)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=1, autotune=True, batch_hint=4)
+    th = synthetic.default_angles(spec.n_angles)
+    sino = torch.from_numpy(synthetic.sinogram(spec, th).astype(np.float32)).cuda()
+    alone = plan.reconstruct(sino)
+    batch = fbp.Batch([plan, plan], [sino, sino.clone()])
+    batch.launch()
+    torch.cuda.synchronize()
+    got = alone.cpu().numpy()
+    assert np.array_equal(got, batch.images[0].cpu().numpy())
+    assert np.array_equal(got, batch.images[1].cpu().numpy())
+    ref = oracle.fbp(sino.double().cpu().numpy(), th, 1.0, 1, spec.n_pix, nthreads=16)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-4 * scale
+    assert np.sqrt(np.mean((got - ref) ** 2)) <= 2e-5 * scale
+
+
+def test_angle_chunk_does_not_change_bits(fbp):
+    import torch
+    spec = synthetic.SliceSpec(96, 150, synthetic.det_for(96), 5, seed=72)
+    sino = torch.from_numpy(synthetic.sinogram(spec).astype(np.float32)).cuda()
+    imgs = []
+    for ch in (8, 16, 32):
+        plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, angle_chunk=ch)
+        imgs.append(plan.reconstruct(sino).cpu().numpy())
+    assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[1], imgs[2])
+
+
+def test_tuning_cache_file_survives_processes(fbp, tmp_path):
+    cache = tmp_path / "tune.txt"
+    code = ("import sys, json; sys.path.insert(0, %r); import paper_2109_02174_gb300 as f; "
+            "print(json.dumps(f.fbp_autotune(64, 90, 92, batch=2)))" % ROOT)
+    env = dict(os.environ, FBP_TUNE_CACHE=str(cache))
+    out1 = json.loads(subprocess.check_output([sys.executable, "-c", code], env=env).decode()
+                      .strip().splitlines()[-1])
+    assert out1["from_cache"] == 0 and cache.exists()
+    assert len(cache.read_text().strip().splitlines()) == 1
+    out2 = json.loads(subprocess.check_output([sys.executable, "-c", code], env=env).decode()
+                      .strip().splitlines()[-1])
+    assert out2["from_cache"] == 1
+    assert out2["tile_x"] == out1["tile_x"] and out2["filter_path"] == out1["filter_path"]
