@@ -70,13 +70,27 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
         }
         cudaError_t e = launch_filter_fft_many(plans, sinos.data(), lds.data(), qs.data(), n, s);
         if (e != cudaSuccess) return e;
+        // Toeplitz-route slices: one launch per plan (they share its T tables)
+        std::map<const Plan *, std::vector<int>> by_plan;
+        for (int i = 0; i < n; ++i)
+            if (plans[i]->filter_path == FBP_PATH_TOEPLITZ_TC) by_plan[plans[i]].push_back(i);
+        for (auto &kv : by_plan) {
+            std::vector<const float *> ss;
+            std::vector<int> ll;
+            std::vector<float *> qq;
+            for (int i : kv.second) {
+                ss.push_back(sinos[(size_t)i]);
+                ll.push_back(lds[(size_t)i]);
+                qq.push_back(static_cast<float *>(qs[(size_t)i]));
+            }
+            e = launch_filter_tc_many(*kv.first, ss.data(), ll.data(), qq.data(),
+                                      (int)ss.size(), s);
+            if (e != cudaSuccess) return e;
+        }
         for (int i = 0; i < n; ++i) {
             const Plan &p = *plans[i];
-            if (p.filter_path == FBP_PATH_FFT) continue;
-            e = (p.filter_path == FBP_PATH_TOEPLITZ_TC)
-                    ? launch_filter_tc(p, sinos[(size_t)i], lds[(size_t)i],
-                                       static_cast<float *>(qs[(size_t)i]), s)
-                    : launch_filter_direct(p, sinos[(size_t)i], lds[(size_t)i], qs[(size_t)i], s);
+            if (p.filter_path != FBP_PATH_DIRECT) continue;
+            e = launch_filter_direct(p, sinos[(size_t)i], lds[(size_t)i], qs[(size_t)i], s);
             if (e != cudaSuccess) return e;
         }
     }

@@ -6,12 +6,14 @@
 // x_lo = x - x_hi, and P T ~= P_hi T_hi + P_hi T_lo + P_lo T_hi, each product
 // accumulated in FP32 in tensor memory.  T_hi and T_lo are plan tables.
 //
-// One CTA per 128 x 128 output tile (rows m0.., output bins n0 = 126 t - 1 ..):
+// One CTA per 128 x 128 output tile (rows m0.., output bins n0 = 126 t - 1 ..)
+// of one slice; one launch covers every slice that shares the plan:
 //   warp 0 (lane 0) issues tcgen05.mma, K-chunk after K-chunk (32 columns);
 //   warp 1 (lane 0) brings T_hi/T_lo tiles in with 2D TMA (128-byte swizzle);
-//   warps 2..5 load the sinogram rows with coalesced loads, split them into
+//   warps 2..9 load the sinogram rows with coalesced loads (the next chunk's
+//   values are in flight while the current ones are stored), split them into
 //   tf32 hi/lo and store both in the same swizzled layout, then run the
-//   epilogue: tcgen05.ld of the accumulator, (mid, slope) pairs of
+//   epilogue: tcgen05.ld of the accumulators, (mid, slope) pairs of
 //   consecutive bins, stores to the filtered rows.
 // Tiles step by 126 output pairs and overlap by two columns so every pair's
 // two bins sit in one tile; the row n0 = -1 of the first tile is out of bounds
@@ -26,6 +28,8 @@
 #include "filter_tc.cuh"
 #include "ptx.cuh"
 
+#include <cstring>
+
 namespace fbp {
 namespace {
 
@@ -37,7 +41,9 @@ constexpr int kStages = 3;
 constexpr int kAcc = 4;       // accumulators (TMEM column blocks), K-chunks round-robin
 constexpr int kTile = kBM * kBK * 4;          // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTile;        // A_hi, A_lo, B_hi, B_lo
-constexpr int kThreads = 192;
+constexpr int kLoadWarps = 8;  // warps 2..9: sinogram split, then epilogue
+constexpr int kThreads = 32 * (2 + kLoadWarps);
+constexpr int kRowsPerLoader = kBM / kLoadWarps;  // 16
 
 __device__ __forceinline__ uint32_t tf32_rna(float x)
 {
@@ -109,14 +115,52 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Epilogue of one warp: TMEM lane quarter `quarter`, half H of the tile's 126
+// pairs (H = 0: pairs 0..63 from columns 0..95; H = 1: pairs 64..125 from
+// columns 64..127).  Column j holds Q[n0 + j]; pair p0 + j takes columns j, j+1.
+template <int H>
+__device__ __forceinline__ void epilogue_half(uint32_t tmem, int quarter, int used, float *row,
+                                              bool valid_row, int p0, int npairs)
+{
+    constexpr int C0 = H ? 2 : 0;  // first 32-column chunk
+    constexpr int NC = H ? 2 : 3;  // chunks loaded
+    constexpr int J0 = H ? 64 : 0;
+    constexpr int J1 = H ? kStep : 64;
+    float v[NC][32];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        const uint32_t lane_col = ((uint32_t)(quarter * 32) << 16) + (uint32_t)((C0 + cc) * 32);
+        tmem_ld32(tmem + lane_col, v[cc]);
+        for (int a = 1; a < used; ++a) {
+            float w[32];
+            tmem_ld32(tmem + lane_col + (uint32_t)(a * kBN), w);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[cc][j] += w[j];
+        }
+    }
+    if (!valid_row) return;
+#pragma unroll
+    for (int j = J0; j < J1; j += 2) {
+        if (p0 + j < npairs) {
+            const int l = j - C0 * 32;
+            const float a0 = v[l / 32][l % 32];
+            const float a1 = v[(l + 1) / 32][(l + 1) % 32];
+            const float a2 = v[(l + 2) / 32][(l + 2) % 32];
+            *reinterpret_cast<float4 *>(row + 2 * (p0 + j)) =
+                make_float4((a0 + a1) * 0.5f, a1 - a0, (a1 + a2) * 0.5f, a2 - a1);
+        }
+    }
+}
+
 struct TcArgs {
-    const float *sino;
-    float *q;  // filtered pairs [A][pitch]
-    int ld;
+    const float *sino[kTcMaxSlices];
+    float *q[kTcMaxSlices];  // filtered pairs [A][pitch]
+    int ld[kTcMaxSlices];
     int A;
     int D;
     int pitch;
-    int nk;  // K chunks
+    int nk;       // K chunks
+    int m_tiles;  // row tiles per slice
     int *status;
 };
 
@@ -138,12 +182,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int n_tile = blockIdx.x;
-    const int m0 = blockIdx.y * kBM;
+    const int sl = blockIdx.y / args.m_tiles;
+    const int m0 = (blockIdx.y - sl * args.m_tiles) * kBM;
+    const float *sino = args.sino[sl];
+    const int ld = args.ld[sl];
     const int n0 = n_tile * kStep - 1;  // first output bin of the tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(bar_full_a + 8 * s, 128);
+            mbar_init(bar_full_a + 8 * s, 32 * kLoadWarps);
             mbar_init(bar_full_b + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
@@ -216,10 +263,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         // -------------------------------------------------------- A split, then epilogue
-        const int cw = warp - 2;  // 0..3: rows 32 cw .. 32 cw + 31 of the tile
+        const int cw = warp - 2;  // rows 16 cw .. 16 cw + 15 of the tile
+        float cur[kRowsPerLoader], nxt[kRowsPerLoader];
+        auto load_chunk = [&](int kc, float (&v)[kRowsPerLoader]) {
+            const int k = kc * kBK + lane;
+#pragma unroll
+            for (int i = 0; i < kRowsPerLoader; ++i) {
+                const int m = m0 + cw * kRowsPerLoader + i;
+                v[i] = (m < args.A && k < args.D) ? __ldg(&sino[(size_t)m * ld + k]) : 0.0f;
+            }
+        };
+        if (args.nk > 0) load_chunk(0, cur);
         for (int kc = 0; kc < args.nk; ++kc) {
             const int s = kc % kStages;
             const uint32_t use = (uint32_t)(kc / kStages);
+            if (kc + 1 < args.nk) load_chunk(kc + 1, nxt);
             if (*abort_flag) break;
             if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u)) {
                 fail();
@@ -227,14 +285,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             unsigned char *a_hi = bp + s * kStageBytes;
             unsigned char *a_lo = a_hi + kTile;
-            const int k = kc * kBK + lane;
-#pragma unroll 8
-            for (int i = 0; i < 32; ++i) {
-                const int r = cw * 32 + i;
-                const int m = m0 + r;
-                const float x = (m < args.A && k < args.D) ? __ldg(&args.sino[(size_t)m * args.ld + k]) : 0.0f;
-                const uint32_t hi = tf32_rna(x);
-                const float lo = x - __uint_as_float(hi);
+#pragma unroll
+            for (int i = 0; i < kRowsPerLoader; ++i) {
+                const int r = cw * kRowsPerLoader + i;
+                const uint32_t hi = tf32_rna(cur[i]);
+                const float lo = cur[i] - __uint_as_float(hi);
                 // 128-byte swizzle: 16-byte chunk (lane / 4) XOR (row mod 8)
                 const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 +
                                                 ((((lane >> 2) ^ (r & 7)) << 4) | ((lane & 3) << 2)));
@@ -243,44 +298,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             fence_proxy_async_smem();  // generic-proxy stores -> tensor-core reads
             mbar_arrive_cta(bar_full_a + 8 * s);
+#pragma unroll
+            for (int i = 0; i < kRowsPerLoader; ++i) cur[i] = nxt[i];
         }
-        // epilogue: this warp owns TMEM lanes 32 (warp % 4) .. +31 = tile rows
+        // epilogue: this warp owns TMEM lanes 32 (warp % 4) .. +31 = tile rows and,
+        // with the other warp of its lane quarter, half of the tile's pairs:
+        // half 0 emits pairs 0..63 from columns 0..95, half 1 pairs 64..125
+        // from columns 64..127.
         const int quarter = warp & 3;
+        const int half = (warp - 2) / 4;
         const int r = quarter * 32 + lane;
         const int m = m0 + r;
         const bool ok = mbar_wait_bounded(bar_acc, 0);
         if (!ok) fail();
         tc_fence_after();
         if (ok && !*abort_flag) {
-            // column j holds Q[n0 + j]; pair p = 126 t + j takes columns j, j + 1
-            float v[kBN / 32][32];
             const int used = args.nk < kAcc ? args.nk : kAcc;  // accumulators written
-#pragma unroll
-            for (int c = 0; c < kBN / 32; ++c) {
-                const uint32_t lane_col = ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32);
-                tmem_ld32(tmem + lane_col, v[c]);
-                for (int a = 1; a < used; ++a) {
-                    float w[32];
-                    tmem_ld32(tmem + lane_col + (uint32_t)(a * kBN), w);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[c][j] += w[j];
-                }
-            }
-            if (m < args.A) {
-                float *row = args.q + (size_t)m * args.pitch;
-                const int p0 = n_tile * kStep;  // even: float4 = two pairs, 16-byte aligned
-                const int npairs = args.pitch / 2;
-#pragma unroll
-                for (int j = 0; j < kStep; j += 2) {
-                    if (p0 + j < npairs) {
-                        const float a0 = v[j / 32][j % 32];
-                        const float a1 = v[(j + 1) / 32][(j + 1) % 32];
-                        const float a2 = v[(j + 2) / 32][(j + 2) % 32];
-                        *reinterpret_cast<float4 *>(row + 2 * (p0 + j)) =
-                            make_float4((a0 + a1) * 0.5f, a1 - a0, (a1 + a2) * 0.5f, a2 - a1);
-                    }
-                }
-            }
+            float *row = args.q[sl] + (size_t)(m < args.A ? m : 0) * args.pitch;
+            if (half == 0)
+                epilogue_half<0>(tmem, quarter, used, row, m < args.A, n_tile * kStep,
+                                 args.pitch / 2);
+            else
+                epilogue_half<1>(tmem, quarter, used, row, m < args.A, n_tile * kStep,
+                                 args.pitch / 2);
         }
     }
 
@@ -298,24 +338,39 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t filter_tc_smem_bytes() { return (size_t)kStages * kStageBytes + 8 * (3 * kStages + 1) + 16 + 1024; }
 
-cudaError_t launch_filter_tc(const Plan &p, const float *sino, int ld, float *q, cudaStream_t s)
+cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, const int *lds,
+                                  float *const *qs, int n, cudaStream_t s)
 {
-    TcArgs a;
-    a.sino = sino;
-    a.q = q;
-    a.ld = ld;
-    a.A = p.A;
-    a.D = p.D;
-    a.pitch = p.pitch;
-    a.nk = (p.D + kBK - 1) / kBK;
-    a.status = p.d_status;
     const size_t smem = filter_tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(filter_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((p.pitch / 2 + kStep - 1) / kStep, (p.A + kBM - 1) / kBM);
-    filter_tc_kernel<<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);
-    return cudaGetLastError();
+    for (int b = 0; b < n; b += kTcMaxSlices) {
+        const int cnt = (n - b < kTcMaxSlices) ? n - b : kTcMaxSlices;
+        TcArgs a;
+        std::memset(&a, 0, sizeof a);
+        for (int i = 0; i < cnt; ++i) {
+            a.sino[i] = sinos[b + i];
+            a.q[i] = qs[b + i];
+            a.ld[i] = lds[b + i];
+        }
+        a.A = p.A;
+        a.D = p.D;
+        a.pitch = p.pitch;
+        a.nk = (p.D + kBK - 1) / kBK;
+        a.m_tiles = (p.A + kBM - 1) / kBM;
+        a.status = p.d_status;
+        dim3 grid((p.pitch / 2 + kStep - 1) / kStep, a.m_tiles * cnt);
+        filter_tc_kernel<<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_filter_tc(const Plan &p, const float *sino, int ld, float *q, cudaStream_t s)
+{
+    return launch_filter_tc_many(p, &sino, &ld, &q, 1, s);
 }
 
 }  // namespace fbp

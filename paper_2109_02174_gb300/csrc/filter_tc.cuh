@@ -15,7 +15,12 @@ struct TcTables {
     int kpad;
 };
 
+constexpr int kTcMaxSlices = 64;  // slices of one plan per launch
+
 size_t filter_tc_smem_bytes();
 cudaError_t launch_filter_tc(const Plan &p, const float *sino, int ld, float *q, cudaStream_t s);
+// Every slice of `n` that uses plan p in as few launches as possible.
+cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, const int *lds,
+                                  float *const *qs, int n, cudaStream_t s);
 
 }  // namespace fbp

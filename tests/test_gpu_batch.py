@@ -98,9 +98,10 @@ def test_batch_mixes_kernel_configurations(fbp):
     import torch
     n, A = 96, 60
     D = synthetic.det_for(n)
+    tc = fbp.Plan(n, A, D, filter_path=1)
     plans = [fbp.Plan(n, A, D), fbp.Plan(n, A, 2 * D, det_spacing=0.45),
              fbp.Plan(n, A, D, q_storage=2), fbp.Plan(n, A, D, accumulate=1),
-             fbp.Plan(n, A, D, tile_x=8, tile_y=32)]
+             fbp.Plan(n, A, D, tile_x=8, tile_y=32), tc, tc, fbp.Plan(n, A, D, filter_path=3)]
     specs = [synthetic.SliceSpec(n, A, p.n_det, 5, seed=900 + i, tau=p.det_spacing)
              for i, p in enumerate(plans)]
     sinos = [_sino(s) for s in specs]
