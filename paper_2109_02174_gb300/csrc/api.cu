@@ -135,6 +135,7 @@ BpConfig bp_config(const Plan &p)
     c.wx = p.bp_wx;
     c.wy = p.bp_wy;
     c.chunk = p.bp_chunk;
+    c.group = 1;
     c.half_pairs = p.q_storage == FBP_F16;
     c.kahan = p.accumulate == FBP_ACC_KAHAN;
     return c;

@@ -79,11 +79,11 @@ struct Layout {
     int full;   // offset of full barriers [NSTAGE]
     int empty;  // offset of empty barriers [NSTAGE]
     int total;  // bytes including 128 of alignment slack
-    __host__ __device__ static Layout make(int wp_max, int pair_bytes)
+    __host__ __device__ static Layout make(int wp_max, int pair_bytes, int group)
     {
         Layout L;
         L.row = ((wp_max * pair_bytes + 127) / 128) * 128;
-        L.stage = CH * L.row;
+        L.stage = group * CH * L.row;
         L.prm = NSTAGE * L.stage;
         L.full = L.prm + NSTAGE * CH * 16;
         L.empty = L.full + NSTAGE * 8;
@@ -104,21 +104,22 @@ __device__ __forceinline__ int2 item_of(const BpLaunch<MAXS> &P, int item)
     return make_int2(lo, item - (lo > 0 ? P.tile_end[lo - 1] : 0));
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int CH, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS>
 __global__ void __launch_bounds__(32 * (WX * WY + 1))
     bp_persistent_kernel(const __grid_constant__ BpLaunch<MAXS> P)
 {
+    static_assert(G == 1 || (G == 2 && !KAHAN), "two-slice items are plain-sum only");
     constexpr int NCW = WX * WY;           // consumer warps
     constexpr int TX = 8 * WX;             // tile width  (warp footprint 8 wide)
     constexpr int TY = 32 * WY;            // tile height (warp covers 32 rows)
     constexpr int PPT = 8;                 // pixels per consumer thread (rows ly0 + 4j)
-    constexpr int NSTAGE = bp_stages(CH);
+    constexpr int NSTAGE = bp_stages(CH, G);
     using TR = PairTraits<PairT>;
     using L_t = Layout<NSTAGE, CH>;
     static_assert(CH <= 32, "one producer lane per angle of a chunk");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const L_t L = L_t::make(P.wp_max, TR::kBytes);
+    const L_t L = L_t::make(P.wp_max, TR::kBytes, G);
     const uint32_t base_addr = (smem_addr(smem) + 127u) & ~127u;
     unsigned char *base_ptr = smem + (base_addr - smem_addr(smem));
     float4 *prm = reinterpret_cast<float4 *>(base_ptr + L.prm);
@@ -143,7 +144,6 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
         for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
             const int2 wi = item_of(P, item);
             const BpSlice &S = P.slices[wi.x];
-            const CUtensorMap *map = &P.maps[wi.x];
             const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
             const double x0 = (double)(tx * TX) - S.half_n;
             const double y0 = (double)(ty * TY) - S.half_n;
@@ -175,13 +175,16 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
                 __syncwarp();
                 if (lane == 0) {
                     const uint32_t bar = full0 + 8u * s;
-                    mbar_arrive_expect_tx(bar, (uint32_t)(na * S.wp * TR::kBytes));
+                    mbar_arrive_expect_tx(bar, (uint32_t)(G * na * S.wp * TR::kBytes));
                 }
                 __syncwarp();
-                // each lane issues its own angle's load (x in elements of PairT)
+                // each lane issues its own angle's load(s) (x in elements of PairT);
+                // slice g of the item lands in rows g*CH .. g*CH + CH-1 of the stage
                 if (lane < na) {
-                    tma_load_2d(base_addr + (uint32_t)(s * L.stage + lane * L.row), map,
-                                2 * pb, a0 + lane, full0 + 8u * s);
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        tma_load_2d(base_addr + (uint32_t)(s * L.stage + (g * CH + lane) * L.row),
+                                    &P.maps[G * wi.x + g], 2 * pb, a0 + lane, full0 + 8u * s);
                 }
             }
         }
@@ -206,10 +209,12 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
         const BpSlice &S = P.slices[wi.x];
         const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
         const int nch = (S.A + CH - 1) / CH;
-        float acc[PPT];
+        float acc[G][PPT];
         float cmp[KAHAN ? PPT : 1];
 #pragma unroll
-        for (int j = 0; j < PPT; ++j) acc[j] = 0.0f;
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) acc[g][j] = 0.0f;
 #pragma unroll
         for (int j = 0; j < (KAHAN ? PPT : 1); ++j) cmp[j] = 0.0f;
 
@@ -240,28 +245,32 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
                     const float2 w = __ffma2_rn(kf, kNeg1, v);
                     const uint32_t o0 = (__float_as_uint(t.x) << TR::kShift) + cb;
                     const uint32_t o1 = (__float_as_uint(t.y) << TR::kShift) + cb;
-                    float2 q0, q1;
-                    if constexpr (TR::kBytes == 8) {
-                        q0 = lds_f2(o0);
-                        q1 = lds_f2(o1);
-                    } else {
-                        q0 = lds_h2_as_f2(o0);
-                        q1 = lds_h2_as_f2(o1);
-                    }
-                    const float v0 = fmaf(w.x, q0.y, q0.x);
-                    const float v1 = fmaf(w.y, q1.y, q1.x);
-                    if constexpr (KAHAN) {
-                        const float y0 = v0 - cmp[2 * jj];
-                        const float t0 = acc[2 * jj] + y0;
-                        cmp[2 * jj] = (t0 - acc[2 * jj]) - y0;
-                        acc[2 * jj] = t0;
-                        const float y1 = v1 - cmp[2 * jj + 1];
-                        const float t1 = acc[2 * jj + 1] + y1;
-                        cmp[2 * jj + 1] = (t1 - acc[2 * jj + 1]) - y1;
-                        acc[2 * jj + 1] = t1;
-                    } else {
-                        acc[2 * jj] += v0;
-                        acc[2 * jj + 1] += v1;
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const uint32_t go = (uint32_t)(g * CH * L.row);
+                        float2 q0, q1;
+                        if constexpr (TR::kBytes == 8) {
+                            q0 = lds_f2(o0 + go);
+                            q1 = lds_f2(o1 + go);
+                        } else {
+                            q0 = lds_h2_as_f2(o0 + go);
+                            q1 = lds_h2_as_f2(o1 + go);
+                        }
+                        const float v0 = fmaf(w.x, q0.y, q0.x);
+                        const float v1 = fmaf(w.y, q1.y, q1.x);
+                        if constexpr (KAHAN) {
+                            const float y0 = v0 - cmp[2 * jj];
+                            const float t0 = acc[0][2 * jj] + y0;
+                            cmp[2 * jj] = (t0 - acc[0][2 * jj]) - y0;
+                            acc[0][2 * jj] = t0;
+                            const float y1 = v1 - cmp[2 * jj + 1];
+                            const float t1 = acc[0][2 * jj + 1] + y1;
+                            cmp[2 * jj + 1] = (t1 - acc[0][2 * jj + 1]) - y1;
+                            acc[0][2 * jj + 1] = t1;
+                        } else {
+                            acc[g][2 * jj] += v0;
+                            acc[g][2 * jj + 1] += v1;
+                        }
                     }
                 }
             }
@@ -272,20 +281,24 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1))
         const int col = tx * TX + lx;
         if (col < S.n) {
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                const int row = ty * TY + ly0 + 4 * j;
-                if (row < S.n) S.image[(size_t)row * S.n + col] = acc[j] * S.scale;
+            for (int g = 0; g < G; ++g) {
+                float *img = g ? S.image2 : S.image;
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const int row = ty * TY + ly0 + 4 * j;
+                    if (row < S.n) img[(size_t)row * S.n + col] = acc[g][j] * S.scale;
+                }
             }
         }
     }
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int CH, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS>
 cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
 {
-    using L_t = Layout<bp_stages(CH), CH>;
-    const L_t L = L_t::make(P.wp_max, PairTraits<PairT>::kBytes);
-    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, CH, MAXS>;
+    using L_t = Layout<bp_stages(CH, G), CH>;
+    const L_t L = L_t::make(P.wp_max, PairTraits<PairT>::kBytes, G);
+    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, CH, G, MAXS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          L.total);
     if (e != cudaSuccess) return e;
@@ -304,22 +317,31 @@ cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int G, int MAXS>
 cudaError_t by_chunk(const BpLaunch<MAXS> &P, int chunk, int grid_limit, cudaStream_t s)
 {
-    if (chunk == 8) return launch_one<PairT, KAHAN, WX, WY, 8, MAXS>(P, grid_limit, s);
-    if (chunk == 32) return launch_one<PairT, KAHAN, WX, WY, 32, MAXS>(P, grid_limit, s);
-    if (chunk == 16) return launch_one<PairT, KAHAN, WX, WY, 16, MAXS>(P, grid_limit, s);
+    if (chunk == 8) return launch_one<PairT, KAHAN, WX, WY, 8, G, MAXS>(P, grid_limit, s);
+    if (chunk == 32) return launch_one<PairT, KAHAN, WX, WY, 32, G, MAXS>(P, grid_limit, s);
+    if (chunk == 16) return launch_one<PairT, KAHAN, WX, WY, 16, G, MAXS>(P, grid_limit, s);
     return cudaErrorInvalidValue;
 }
 
 template <int WX, int WY, int MAXS>
 cudaError_t by_variant(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit, cudaStream_t s)
 {
-    if (!c.half_pairs && !c.kahan) return by_chunk<float, false, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
-    if (!c.half_pairs && c.kahan) return by_chunk<float, true, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
-    if (c.half_pairs && !c.kahan) return by_chunk<__half, false, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
-    return by_chunk<__half, true, WX, WY, MAXS>(P, c.chunk, grid_limit, s);
+    if (c.group == 2) {
+        if constexpr (MAXS > 1) {
+            if (c.kahan) return cudaErrorInvalidValue;
+            if (!c.half_pairs)
+                return by_chunk<float, false, WX, WY, 2, MAXS>(P, c.chunk, grid_limit, s);
+            return by_chunk<__half, false, WX, WY, 2, MAXS>(P, c.chunk, grid_limit, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (!c.half_pairs && !c.kahan) return by_chunk<float, false, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
+    if (!c.half_pairs && c.kahan) return by_chunk<float, true, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
+    if (c.half_pairs && !c.kahan) return by_chunk<__half, false, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
+    return by_chunk<__half, true, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
 }
 
 template <int MAXS>

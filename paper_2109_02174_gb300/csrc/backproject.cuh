@@ -7,14 +7,20 @@
 
 namespace fbp {
 
-// Shared-memory ring: stages of `chunk` angles each, 64 angles in flight.
-__host__ __device__ constexpr int bp_stages(int chunk) { return chunk >= 32 ? 2 : 64 / chunk; }
+// Shared-memory ring: stages of `chunk` angles (of every slice of an item), 64
+// window rows in flight, at least two stages.
+__host__ __device__ constexpr int bp_stages(int chunk, int group)
+{
+    return chunk * group >= 32 ? 2 : 64 / (chunk * group);
+}
 constexpr int kBpMaxSlices = 64;  // slices per batched launch (tensor maps in the parameters)
 
-// One slice of a launch.
+// One work-list entry of a launch: a slice, or (group = 2) two slices of the
+// same plan that share every index computation.
 struct BpSlice {
     const double2 *trig64;  // (cos, sin) / tau per angle
     float *image;           // [n][n]
+    float *image2;          // second slice of a group (group = 2), else unused
     int n;
     int A;
     int wp;       // detector window per tile and angle, in (mid, slope) pairs
@@ -32,7 +38,7 @@ struct BpSlice {
 // are handed out first.
 template <int MAXS>
 struct BpLaunch {
-    CUtensorMap maps[MAXS];
+    CUtensorMap maps[2 * MAXS];  // entry s, slice g of its group: maps[group * s + g]
     BpSlice slices[MAXS];
     int tile_end[MAXS];  // inclusive prefix sums of the slices' tile counts
     int n_slices;
@@ -48,6 +54,7 @@ struct BpConfig {
     int chunk;        // angles per stage: 8, 16 or 32
     bool half_pairs;  // FP16-stored (mid, slope) pairs
     bool kahan;       // Kahan-compensated sum over angles
+    int group;        // slices per work item: 1, or 2 (same plan, not Kahan)
 };
 
 cudaError_t launch_backproject(const BpLaunch<1> &P, const BpConfig &c, cudaStream_t s);

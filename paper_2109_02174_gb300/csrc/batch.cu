@@ -105,22 +105,65 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
         std::vector<int> members = kv.second;
         std::stable_sort(members.begin(), members.end(),
                          [&](int a, int c) { return plans[a]->A > plans[c]->A; });
-        std::memset(L.get(), 0, sizeof(*L));
-        int acc = 0;
-        for (size_t m = 0; m < members.size(); ++m) {
-            const int i = members[m];
-            const Plan &p = *plans[i];
-            if (!encode_pairs_map(p, io[i].workspace, &L->maps[m])) return cudaErrorInvalidValue;
-            L->slices[m] = slice_desc(p, static_cast<float *>(io[i].image));
-            acc += tiles_of(p);
-            L->tile_end[m] = acc;
-            L->wp_max = std::max(L->wp_max, p.bp_wp);
+        const BpConfig cfg = bp_config(*plans[members[0]]);
+        // Slices of one plan share every index computation: pair them into
+        // two-slice items (plain sums only); the rest stay single.
+        std::vector<std::pair<int, int>> pairs;
+        std::vector<int> singles;
+        if (!cfg.kahan) {
+            std::map<const Plan *, std::vector<int>> by_plan;
+            for (int i : members) by_plan[plans[i]].push_back(i);
+            std::vector<bool> paired((size_t)n, false);
+            for (int i : members) {
+                if (paired[(size_t)i]) continue;
+                std::vector<int> &same = by_plan[plans[i]];
+                int mate = -1;
+                for (int j : same)
+                    if (j != i && !paired[(size_t)j]) {
+                        mate = j;
+                        break;
+                    }
+                if (mate >= 0) {
+                    paired[(size_t)i] = paired[(size_t)mate] = true;
+                    pairs.push_back(std::make_pair(i, mate));
+                } else {
+                    singles.push_back(i);
+                }
+            }
+        } else {
+            singles = members;
         }
-        L->n_slices = (int)members.size();
-        L->n_items = acc;
-        L->status = status;
-        cudaError_t e = launch_backproject_batch(*L, bp_config(*plans[members[0]]), 0, s);
-        if (e != cudaSuccess) return e;
+        for (int group = 2; group >= 1; --group) {
+            const int count = group == 2 ? (int)pairs.size() : (int)singles.size();
+            for (int b = 0; b < count; b += kBpMaxSlices) {
+                const int cnt = std::min(kBpMaxSlices, count - b);
+                std::memset(L.get(), 0, sizeof(*L));
+                int acc = 0;
+                for (int m = 0; m < cnt; ++m) {
+                    const int i = group == 2 ? pairs[(size_t)(b + m)].first : singles[(size_t)(b + m)];
+                    const Plan &p = *plans[i];
+                    if (!encode_pairs_map(p, io[i].workspace, &L->maps[group * m]))
+                        return cudaErrorInvalidValue;
+                    L->slices[m] = slice_desc(p, static_cast<float *>(io[i].image));
+                    if (group == 2) {
+                        const int j = pairs[(size_t)(b + m)].second;
+                        if (!encode_pairs_map(*plans[j], io[j].workspace, &L->maps[2 * m + 1]))
+                            return cudaErrorInvalidValue;
+                        L->slices[m].image2 = static_cast<float *>(io[j].image);
+                    }
+                    acc += tiles_of(p);
+                    L->tile_end[m] = acc;
+                    L->wp_max = std::max(L->wp_max, p.bp_wp);
+                }
+                L->n_slices = cnt;
+                L->n_items = acc;
+                L->status = status;
+                BpConfig c = cfg;
+                c.group = group;
+                cudaError_t e = launch_backproject_batch(*L, c, 0, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
     }
     return cudaSuccess;
 }

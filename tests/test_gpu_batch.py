@@ -112,6 +112,25 @@ def test_batch_mixes_kernel_configurations(fbp):
         assert np.array_equal(img.cpu().numpy(), _alone(fbp, plan, sino))
 
 
+@pytest.mark.parametrize("q_storage", [0, 2])
+def test_same_plan_slices_pair_up_bitwise(fbp, q_storage):
+    """Slices sharing a plan go through two-slice work items (one index
+    computation for both); an odd one out stays single.  Each image equals its
+    alone result bit for bit."""
+    import torch
+    n, A = 150, 96
+    D = synthetic.det_for(n)
+    plan = fbp.Plan(n, A, D, q_storage=q_storage, angle_chunk=16)
+    specs = [synthetic.SliceSpec(n, A, D, 6, seed=950 + i) for i in range(5)]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch([plan] * 5, sinos)
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.status()
+    for sino, img in zip(sinos, batch.images):
+        assert np.array_equal(img.cpu().numpy(), _alone(fbp, plan, sino))
+
+
 def test_batched_uneven_workload_64(fbp):
     """The batched configuration: 64 uneven slices (n in {256,384,512,768},
     A in {180,360,720,1440}) in one graph.  Every slice is bit-identical to its
