@@ -147,6 +147,23 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ ranks
+def shard_ids(rank: int, world: int, per_rank: int) -> list[int]:
+    """Slice ids of one rank: replicas with disjoint phantoms (weak scaling,
+    no data exchanged between ranks)."""
+    return [rank * per_rank + i for i in range(per_rank)]
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The timed region's length over all ranks (the slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ our arm
 def _timed(fn, steps, stream, per_launch=False):
     """Run fn() `steps` times between CUDA events on `stream`; returns total ms
@@ -268,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     S = args.slices
-    specs = [workload_spec(rank * S + i) for i in range(S)]
+    specs = [workload_spec(i) for i in shard_ids(rank, world, S)]
     spec0 = specs[0]
     theta = synthetic.default_angles(spec0.n_angles)
     host = [synthetic.sinogram(s, theta).astype(np.float32) for s in specs]
@@ -304,9 +321,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     full.status()
 
     # ---- the backprojection launch alone over the same buffers (roofline)
@@ -332,10 +347,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_steps = max(args.steps // 4, 5)
     e2e_ms = _timed(lambda: full.run_host(h_sino, h_img), e2e_steps, stream)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     if rank != 0:
         return 0

@@ -48,11 +48,16 @@ def build(force: bool = False) -> str:
 
 
 def _load():
+    """Load liboracle.so.  FBP_ORACLE_LIB may name another build of the same
+    source (the mutation test points it at deliberately broken copies)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            path = os.environ.get("FBP_ORACLE_LIB")
+            if not path:
+                build()
+                path = _LIB
+            lib = ctypes.CDLL(path)
             d = ctypes.POINTER(ctypes.c_double)
             i = ctypes.c_int
             ip = ctypes.POINTER(ctypes.c_int)

@@ -1,0 +1,61 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/fbp_oracle.c (on the CPU),
+builds it, and runs the pin suite against it in a subprocess: the suite must
+fail.  The unmodified source must pass the same way (the control)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fbp_oracle.c")
+
+MUTATIONS = [
+    ("filter without the tau factor", "q[k] = tau * s;", "q[k] = s;"),
+    ("Shepp-Logan denominator sign",
+     "(1.0 - 4.0 * (double)m * (double)m)", "(4.0 * (double)m * (double)m - 1.0)"),
+    ("Ram-Lak odd taps positive", "v = -1.0 / (M_PI * M_PI", "v = 1.0 / (M_PI * M_PI"),
+    ("interpolation weights swapped", "return (1.0 - w) * q0 + w * q1;",
+     "return w * q0 + (1.0 - w) * q1;"),
+    ("x and y transposed in Eq. 2",
+     "double t = x * cos(theta[i]) + y * sin(theta[i]);\n        double u = t / tau",
+     "double t = y * cos(theta[i]) + x * sin(theta[i]);\n        double u = t / tau"),
+    ("angular weight pi/A dropped", "return s * (M_PI / (double)n_angles);", "return s;"),
+    ("detector centre off by half a bin",
+     "double u = t / tau + 0.5 * (double)(n_det - 1);\n        s += interp",
+     "double u = t / tau + 0.5 * (double)n_det;\n        s += interp"),
+    ("splat weights swapped", "if (k >= 0 && k < n_det) p[k] += (1.0 - w) * v;",
+     "if (k >= 0 && k < n_det) p[k] += w * v;"),
+]
+
+
+def _run_pins(lib_path):
+    env = dict(os.environ, FBP_ORACLE_LIB=lib_path)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode
+
+
+def _build(src_text, tmp_path, name):
+    import oracle
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(src_text)
+    subprocess.check_call(["gcc", *oracle.CFLAGS, "-o", str(so), str(c), "-lm", "-lpthread"])
+    return str(so)
+
+
+def test_unmodified_oracle_passes_its_pins(tmp_path):
+    src = open(SRC).read()
+    assert _run_pins(_build(src, tmp_path, "control")) == 0
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    broken = src.replace(old, new, 1)
+    assert _run_pins(_build(broken, tmp_path, "mutant")) != 0, f"pins missed: {name}"
