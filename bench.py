@@ -273,6 +273,43 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
     }
 
 
+def run_uneven(fbp, plan_cache=None):
+    """The batched configuration: 64 uneven slices (n from {256,384,512,768},
+    A from {180,360,720,1440}, D = ceil(n sqrt2)+1, seeds 1000+s) in one graph,
+    against the same slices through one fbp_reconstruct call each."""
+    import torch
+    specs = synthetic.cfg_batch()
+    plans = {}
+    for s in specs:
+        key = (s.n_pix, s.n_angles, s.n_det)
+        if key not in plans:
+            plans[key] = fbp.Plan(*key, filter=s.filter)
+    pl = [plans[(s.n_pix, s.n_angles, s.n_det)] for s in specs]
+    sinos = [torch.from_numpy(synthetic.sinogram(s).astype(np.float32)).cuda() for s in specs]
+    batch = fbp.Batch(pl, sinos)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        batch.launch()
+    torch.cuda.synchronize()
+    steps = 10
+    ms = _timed(batch.launch, steps, stream)
+    batch.status()
+
+    def one_by_one():
+        for p, s, img, ws in zip(pl, sinos, batch.images, batch.workspaces):
+            fbp.fbp_reconstruct(p.handle, s.data_ptr(), s.stride(0), img.data_ptr(),
+                                ws.data_ptr(), int(stream.cuda_stream))
+    one_by_one()
+    plain_ms = _timed(one_by_one, steps, stream)
+    upd = sum(s.updates for s in specs)
+    batch.close()
+    return {"slices": len(specs), "slices_per_s": len(specs) * steps / (ms / 1e3),
+            "gupdates_per_s": upd * steps / (ms / 1e3) / 1e9,
+            "plain_path_slices_per_s": len(specs) * steps / (plain_ms / 1e3),
+            "what": "cfg recipe: 64 slices, n in {256,384,512,768}, A in {180,360,720,1440}, "
+                    "default plans, one captured graph per step"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2109_02174_gb300 as fbp
@@ -402,6 +439,8 @@ def run_ours(args, rank, world, local_rank):
         b.close()
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(fbp, args.serve_seconds)
+    if world == 1 and not args.no_uneven:
+        line["batched_uneven"] = run_uneven(fbp)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -414,6 +453,8 @@ def main():
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the 64-uneven-slice batch measurement")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving run (0 = skip)")
     args = ap.parse_args()

@@ -210,7 +210,8 @@ void make_taps(int kind, int D, double tau, std::vector<double> &out)
 }
 
 // T[n][k] = tau h(n - k), split into tf32 hi (round to nearest, ties away) and
-// the FP32 remainder, rows n < D with stride kpad; plus their TMA maps.
+// the remainder rounded the same way, rows n < D with stride kpad; plus their
+// TMA maps.
 bool make_tc_tables(const Plan &p, const std::vector<double> &taps, TcTables *t)
 {
     const int D = p.D;
@@ -227,7 +228,14 @@ bool make_tc_tables(const Plan &p, const std::vector<double> &taps, TcTables *t)
             float h;
             std::memcpy(&h, &b, 4);
             hi[(size_t)n * t->kpad + k] = h;
-            lo[(size_t)n * t->kpad + k] = (float)(v - (double)h);
+            // the remainder, itself rounded to tf32 (to nearest, ties away)
+            const float r = (float)(v - (double)h);
+            uint32_t rb;
+            std::memcpy(&rb, &r, 4);
+            rb = (rb + 0x1000u) & 0xFFFFE000u;
+            float rl;
+            std::memcpy(&rl, &rb, 4);
+            lo[(size_t)n * t->kpad + k] = rl;
         }
     }
     if (cudaMalloc(&t->d_hi, sizeof(float) * count) != cudaSuccess ||

@@ -20,10 +20,14 @@
 // for TMA and arrives as zeros, which is Q[-1] = 0.  A NSTAGE-deep mbarrier
 // ring (full: data landed, empty: MMAs done reading) keeps loads and MMAs
 // overlapped.  The tensor core's FP32 accumulation loses low bits at every
-// accumulate step, so K-chunks go round-robin to four accumulators (all 512
-// TMEM columns) that the epilogue adds in FP32 registers: each sees a quarter
-// of the steps.  Every wait is bounded; on a timeout the CTA records the
-// status, releases its tensor memory and exits.
+// accumulate step, and a ramp-filtered sinogram row is 50-250 times smaller
+// than the sums it comes from, so partial sums never stay in tensor memory for
+// long: every 32-wide K-chunk gets a fresh accumulator (a ring of four TMEM
+// blocks, all 512 columns) that the epilogue warps add into FP32 registers
+// (correctly rounded) as soon as its MMAs complete, then hand back to the MMA
+// warp.  The lo parts are rounded to tf32 (to nearest) before they reach the
+// tensor core, so its truncation of them leaves no sign-correlated error.  Every wait is bounded; on a timeout the CTA records the status,
+// releases its tensor memory and exits.
 #include "fbp_internal.h"
 #include "filter_tc.cuh"
 #include "ptx.cuh"
@@ -38,7 +42,7 @@ constexpr int kBN = 128;      // output bins per tile (TMEM columns)
 constexpr int kStep = 126;    // output pairs per tile
 constexpr int kBK = 32;       // fp32 elements per 128-byte swizzle row
 constexpr int kStages = 3;
-constexpr int kAcc = 4;       // accumulators (TMEM column blocks), K-chunks round-robin
+constexpr int kAcc = 4;       // accumulator slots (TMEM column blocks), ring
 constexpr int kTile = kBM * kBK * 4;          // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTile;        // A_hi, A_lo, B_hi, B_lo
 constexpr int kLoadWarps = 8;  // warps 2..9: sinogram split, then epilogue
@@ -95,57 +99,67 @@ __device__ __forceinline__ void mbar_arrive_cta(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 16 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
-    uint32_t r[32];
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Epilogue of one warp: TMEM lane quarter `quarter`, half H of the tile's 126
-// pairs (H = 0: pairs 0..63 from columns 0..95; H = 1: pairs 64..125 from
-// columns 64..127).  Column j holds Q[n0 + j]; pair p0 + j takes columns j, j+1.
-template <int H>
-__device__ __forceinline__ void epilogue_half(uint32_t tmem, int quarter, int used, float *row,
-                                              bool valid_row, int p0, int npairs)
+// 1 accumulator column of this thread's lane.
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr)
 {
-    constexpr int C0 = H ? 2 : 0;  // first 32-column chunk
-    constexpr int NC = H ? 2 : 3;  // chunks loaded
-    constexpr int J0 = H ? 64 : 0;
-    constexpr int J1 = H ? kStep : 64;
-    float v[NC][32];
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// Columns an epilogue warp accumulates: half 0 takes columns 0..63 plus
+// column 64 (pairs 0..63), half 1 columns 64..127 (pairs 64..125).  Column j
+// holds Q[n0 + j]; pair p0 + j takes columns j and j + 1.
+template <int H>
+__device__ __forceinline__ void add_block(uint32_t tmem_block, int quarter, float (&sum)[2][32],
+                                          float &extra)
+{
+    constexpr int C0 = H ? 2 : 0;
+    const uint32_t lane_base = tmem_block + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) {
-        const uint32_t lane_col = ((uint32_t)(quarter * 32) << 16) + (uint32_t)((C0 + cc) * 32);
-        tmem_ld32(tmem + lane_col, v[cc]);
-        for (int a = 1; a < used; ++a) {
-            float w[32];
-            tmem_ld32(tmem + lane_col + (uint32_t)(a * kBN), w);
+    for (int cc = 0; cc < 2; ++cc) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[cc][j] += w[j];
+        for (int h = 0; h < 2; ++h) {
+            float w[16];
+            tmem_ld16(lane_base + (uint32_t)((C0 + cc) * 32 + 16 * h), w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum[cc][16 * h + j] += w[j];
         }
     }
-    if (!valid_row) return;
+    if (H == 0) extra += tmem_ld1(lane_base + 64u);
+}
+
+template <int H>
+__device__ __forceinline__ void store_half(const float (&v)[2][32], float extra, float *row, int p0,
+                                           int npairs)
+{
+    constexpr int C0 = H ? 2 : 0;
+    constexpr int J0 = H ? 64 : 0;
+    constexpr int J1 = H ? kStep : 64;
 #pragma unroll
     for (int j = J0; j < J1; j += 2) {
         if (p0 + j < npairs) {
             const int l = j - C0 * 32;
             const float a0 = v[l / 32][l % 32];
             const float a1 = v[(l + 1) / 32][(l + 1) % 32];
-            const float a2 = v[(l + 2) / 32][(l + 2) % 32];
+            const float a2 = (l + 2 < 64) ? v[(l + 2) / 32][(l + 2) % 32] : extra;
             *reinterpret_cast<float4 *>(row + 2 * (p0 + j)) =
                 make_float4((a0 + a1) * 0.5f, a1 - a0, (a1 + a2) * 0.5f, a2 - a1);
         }
@@ -175,8 +189,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar_full_a = base + kStages * kStageBytes;      // [kStages], 128 arrivals
     const uint32_t bar_full_b = bar_full_a + 8 * kStages;          // [kStages], TMA bytes
     const uint32_t bar_empty = bar_full_b + 8 * kStages;           // [kStages], MMA commit
-    const uint32_t bar_acc = bar_empty + 8 * kStages;              // accumulator ready
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bp + kStages * kStageBytes + 8 * (3 * kStages + 1));
+    const uint32_t bar_acc_full = bar_empty + 8 * kStages;         // [kAcc], MMA commit
+    const uint32_t bar_acc_free = bar_acc_full + 8 * kAcc;         // [kAcc], epilogue warps
+    uint32_t *tmem_slot =
+        reinterpret_cast<uint32_t *>(bp + kStages * kStageBytes + 8 * (3 * kStages + 2 * kAcc));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -194,7 +210,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(bar_full_b + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
-        mbar_init(bar_acc, 1);
+        for (int a = 0; a < kAcc; ++a) {
+            mbar_init(bar_acc_full + 8 * a, 1);
+            mbar_init(bar_acc_free + 8 * a, kLoadWarps);
+        }
         *abort_flag = 0;
         fence_proxy_async_smem();
     }
@@ -226,22 +245,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                     fail();
                     break;
                 }
+                const int blk = kc % kAcc;
+                if (kc >= kAcc &&
+                    !mbar_wait_bounded(bar_acc_free + 8 * blk, (uint32_t)(kc / kAcc - 1) & 1u)) {
+                    fail();
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t st = base + s * kStageBytes;
                 const uint32_t a_hi = st, a_lo = st + kTile, b_hi = st + 2 * kTile,
                                b_lo = st + 3 * kTile;
-                const uint32_t d = tmem + (uint32_t)((kc % kAcc) * kBN);
+                const uint32_t d = tmem + (uint32_t)(blk * kBN);
 #pragma unroll
                 for (int kk = 0; kk < kBK / 8; ++kk) {  // K = 8 tf32 = 32 bytes per MMA
                     const uint32_t off = 32u * kk;
-                    const uint32_t acc = (kc >= kAcc || kk > 0) ? 1u : 0u;
-                    mma_tf32(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), acc);
+                    mma_tf32(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), kk > 0 ? 1u : 0u);
                     mma_tf32(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), 1u);
                     mma_tf32(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), 1u);
                 }
-                mma_commit(bar_empty + 8 * s);  // stage s free once these MMAs have read it
+                mma_commit(bar_empty + 8 * s);     // stage s free once these MMAs have read it
+                mma_commit(bar_acc_full + 8 * blk);  // chunk kc's partial sums are ready
             }
-            mma_commit(bar_acc);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -264,6 +288,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // -------------------------------------------------------- A split, then epilogue
         const int cw = warp - 2;  // rows 16 cw .. 16 cw + 15 of the tile
+        const int quarter = warp & 3;   // TMEM lanes 32 quarter .. +31 = tile rows
+        const int half = (warp - 2) / 4;
+        float sum[2][32];
+        float extra = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[c][j] = 0.0f;
+        // Add chunk kc2's accumulator into the FP32 sums, then free it.
+        auto drain = [&](int kc2) -> bool {
+            const int blk = kc2 % kAcc;
+            if (!mbar_wait_bounded(bar_acc_full + 8 * blk, (uint32_t)(kc2 / kAcc) & 1u)) {
+                fail();
+                return false;
+            }
+            tc_fence_after();
+            if (half == 0)
+                add_block<0>(tmem + (uint32_t)(blk * kBN), quarter, sum, extra);
+            else
+                add_block<1>(tmem + (uint32_t)(blk * kBN), quarter, sum, extra);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cta(bar_acc_free + 8 * blk);
+            return true;
+        };
         float cur[kRowsPerLoader], nxt[kRowsPerLoader];
         auto load_chunk = [&](int kc, float (&v)[kRowsPerLoader]) {
             const int k = kc * kBK + lane;
@@ -273,14 +322,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 v[i] = (m < args.A && k < args.D) ? __ldg(&sino[(size_t)m * ld + k]) : 0.0f;
             }
         };
+        bool ok = true;
         if (args.nk > 0) load_chunk(0, cur);
-        for (int kc = 0; kc < args.nk; ++kc) {
+        for (int kc = 0; kc < args.nk && ok; ++kc) {
             const int s = kc % kStages;
             const uint32_t use = (uint32_t)(kc / kStages);
             if (kc + 1 < args.nk) load_chunk(kc + 1, nxt);
-            if (*abort_flag) break;
+            if (*abort_flag) {
+                ok = false;
+                break;
+            }
             if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u)) {
                 fail();
+                ok = false;
                 break;
             }
             unsigned char *a_hi = bp + s * kStageBytes;
@@ -289,38 +343,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < kRowsPerLoader; ++i) {
                 const int r = cw * kRowsPerLoader + i;
                 const uint32_t hi = tf32_rna(cur[i]);
-                const float lo = cur[i] - __uint_as_float(hi);
+                const uint32_t lo = tf32_rna(cur[i] - __uint_as_float(hi));
                 // 128-byte swizzle: 16-byte chunk (lane / 4) XOR (row mod 8)
                 const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 +
                                                 ((((lane >> 2) ^ (r & 7)) << 4) | ((lane & 3) << 2)));
                 *reinterpret_cast<uint32_t *>(a_hi + off) = hi;
-                *reinterpret_cast<float *>(a_lo + off) = lo;
+                *reinterpret_cast<uint32_t *>(a_lo + off) = lo;
             }
             fence_proxy_async_smem();  // generic-proxy stores -> tensor-core reads
             mbar_arrive_cta(bar_full_a + 8 * s);
 #pragma unroll
             for (int i = 0; i < kRowsPerLoader; ++i) cur[i] = nxt[i];
+            if (kc >= 1) ok = drain(kc - 1);  // the previous chunk's MMAs are (nearly) done
         }
-        // epilogue: this warp owns TMEM lanes 32 (warp % 4) .. +31 = tile rows and,
-        // with the other warp of its lane quarter, half of the tile's pairs:
-        // half 0 emits pairs 0..63 from columns 0..95, half 1 pairs 64..125
-        // from columns 64..127.
-        const int quarter = warp & 3;
-        const int half = (warp - 2) / 4;
-        const int r = quarter * 32 + lane;
-        const int m = m0 + r;
-        const bool ok = mbar_wait_bounded(bar_acc, 0);
-        if (!ok) fail();
-        tc_fence_after();
+        if (ok && args.nk > 0) ok = drain(args.nk - 1);
         if (ok && !*abort_flag) {
-            const int used = args.nk < kAcc ? args.nk : kAcc;  // accumulators written
-            float *row = args.q[sl] + (size_t)(m < args.A ? m : 0) * args.pitch;
-            if (half == 0)
-                epilogue_half<0>(tmem, quarter, used, row, m < args.A, n_tile * kStep,
-                                 args.pitch / 2);
-            else
-                epilogue_half<1>(tmem, quarter, used, row, m < args.A, n_tile * kStep,
-                                 args.pitch / 2);
+            const int m = m0 + quarter * 32 + lane;
+            if (m < args.A) {
+                float *row = args.q[sl] + (size_t)m * args.pitch;
+                if (half == 0)
+                    store_half<0>(sum, extra, row, n_tile * kStep, args.pitch / 2);
+                else
+                    store_half<1>(sum, extra, row, n_tile * kStep, args.pitch / 2);
+            }
         }
     }
 
@@ -336,7 +381,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-size_t filter_tc_smem_bytes() { return (size_t)kStages * kStageBytes + 8 * (3 * kStages + 1) + 16 + 1024; }
+size_t filter_tc_smem_bytes()
+{
+    return (size_t)kStages * kStageBytes + 8 * (3 * kStages + 2 * kAcc) + 16 + 1024;
+}
 
 cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, const int *lds,
                                   float *const *qs, int n, cudaStream_t s)
