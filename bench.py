@@ -32,6 +32,8 @@ import synthetic  # noqa: E402
 METRIC = "FBP slices/s and Gupdates/s (pixel×angle) vs plain path; serving p50/p99 ms"
 FP32_LANES_PER_SM = 128
 OPS_PER_UPDATE = 5  # FP32-pipe operations per pixel-angle update in the algorithmic count
+FILTER_PATHS = {"auto": 0, "tc": 1, "fft": 2, "direct": 3}
+ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
 def workload_spec(i: int) -> synthetic.SliceSpec:
@@ -329,7 +331,8 @@ def run_ours(args, rank, world, local_rank):
     # the autotuner picks the filter route and backprojection shape for this
     # geometry on this GPU (timed over a batch; cached in FBP_TUNE_CACHE if set)
     plan = fbp.Plan(spec0.n_pix, spec0.n_angles, spec0.n_det, filter=spec0.filter,
-                    autotune=True, batch_hint=min(S, 64))
+                    autotune=True, batch_hint=min(S, 64),
+                    filter_path=FILTER_PATHS[args.filter_path])
     sinos = [torch.from_numpy(h).to(dev) for h in host]
     works = [plan.empty_workspace() for _ in range(S)]
     images = [plan.empty_image() for _ in range(S)]
@@ -408,8 +411,11 @@ def run_ours(args, rank, world, local_rank):
                        "what": "one fbp_reconstruct call per slice, same slices and stream"},
         "filter_ms_per_step": filt_ms,
         "config": {"workload": WORKLOAD_NAME, "slices_per_step": S * world,
-                   "path": "batched: one captured graph per step (per-slice FFT filters + one "
-                           "persistent backprojection launch over all slices' tiles)",
+                   "path": ("batched: one captured graph per step (%s + one persistent "
+                            "backprojection launch over all slices' tiles)" %
+                            ("per-slice direct filter launches" if plan.filter_path == 3 else
+                             "one %s filter launch over all slices' rows" %
+                             ROUTE_NAMES[plan.filter_path])),
                    "l2": f"inputs larger than L2: {resident_mb:.0f} MB resident per GPU",
                    "tuned": {k: plan.tuning[k] for k in ("filter_path", "fft_len", "tile_x",
                                                          "tile_y", "angle_chunk")},
@@ -455,6 +461,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the 64-uneven-slice batch measurement")
+    ap.add_argument("--filter-path", choices=sorted(FILTER_PATHS), default="auto",
+                    help="ramp-filter route (auto: the autotuner picks)")
     ap.add_argument("--serve-seconds", type=float, default=5.0,
                     help="length of the Poisson serving run (0 = skip)")
     args = ap.parse_args()

@@ -1,6 +1,7 @@
 // Autotuner: picks, per geometry ("shape bucket"), the filter route and the
 // backprojection launch shape (pixel tile, angles per shared-memory stage) by
-// timing them on the device, and caches the choice per GPU model.
+// timing them on the device, and caches the choice per GPU model.  A route
+// fixed in the base options is kept (only the shape is tuned then).
 //
 // The two kernels are independent, so they are tuned separately: every
 // available filter route (FFT, tensor-core Toeplitz, direct) on `batch` slices,
@@ -50,8 +51,8 @@ std::string bucket_key(int n, int A, int D, double tau, int filter, const fbp_op
                        int batch)
 {
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%.9g|%d|%d|%d|%d|%d", gpu_name().c_str(), n, A, D,
-             tau, filter, b.dtype, b.q_storage, b.accumulate, batch);
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%.9g|%d|%d|%d|%d|%d|%d", gpu_name().c_str(), n, A, D,
+             tau, filter, b.dtype, b.q_storage, b.accumulate, b.filter_path, batch);
     return buf;
 }
 
@@ -185,6 +186,7 @@ fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
     // 1. filter routes
     const int paths[3] = {FBP_PATH_FFT, FBP_PATH_TOEPLITZ_TC, FBP_PATH_DIRECT};
     for (int k = 0; k < 3; ++k) {
+        if (b.filter_path != FBP_PATH_AUTO && paths[k] != b.filter_path) continue;
         if (paths[k] == FBP_PATH_TOEPLITZ_TC && b.q_storage != FBP_F32) continue;
         if (paths[k] == FBP_PATH_DIRECT && n_det > 2048) continue;  // O(n_det^2) per row
         fbp_options o = b;

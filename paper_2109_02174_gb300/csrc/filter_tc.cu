@@ -26,8 +26,9 @@
 // blocks, all 512 columns) that the epilogue warps add into FP32 registers
 // (correctly rounded) as soon as its MMAs complete, then hand back to the MMA
 // warp.  The lo parts are rounded to tf32 (to nearest) before they reach the
-// tensor core, so its truncation of them leaves no sign-correlated error.  Every wait is bounded; on a timeout the CTA records the status,
-// releases its tensor memory and exits.
+// tensor core, so its truncation of them leaves no sign-correlated error.
+// Every wait is bounded; on a timeout the CTA records the status, releases its
+// tensor memory and exits.
 #include "fbp_internal.h"
 #include "filter_tc.cuh"
 #include "ptx.cuh"
