@@ -463,7 +463,7 @@ def main():
                     help="skip the 64-uneven-slice batch measurement")
     ap.add_argument("--filter-path", choices=sorted(FILTER_PATHS), default="auto",
                     help="ramp-filter route (auto: the autotuner picks)")
-    ap.add_argument("--serve-seconds", type=float, default=5.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson serving run (0 = skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

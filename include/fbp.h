@@ -212,13 +212,18 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
 fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream);
 
 /*
- * The batch end to end from host memory, all on `stream`: each slice's
- * sinogram (host, [n_angles][n_det] float, contiguous) is copied into the
- * batch's device sinogram buffer, the graph runs, and each image is copied back
- * to host_images[i] ([n_pix][n_pix] float).  One cudaMemcpy2DAsync /
- * cudaMemcpyAsync per slice and direction; host buffers should be pinned for
- * asynchronous copies.  Returns after enqueueing; synchronise the stream
- * before reading the images.
+ * The batch end to end from host memory: each slice's sinogram (host,
+ * [n_angles][n_det] float, contiguous) is copied into the batch's device
+ * sinogram buffer, the slice is reconstructed, and its image is copied back to
+ * host_images[i] ([n_pix][n_pix] float).  The slices are processed in up to
+ * four chunks, pipelined: the sinogram copies run on one internal stream, the
+ * image copies on another, the compute on `stream`, so that chunk c+1 comes in
+ * and chunk c-1 goes out while chunk c computes.  One copy per slice and
+ * direction; host buffers should be pinned for the copies to be asynchronous.
+ * The work starts after what is already on `stream` and `stream` waits for the
+ * last image copy, so synchronising `stream` (or an event recorded on it after
+ * this call) makes every image readable.  Results equal those of
+ * fbp_batch_launch bit for bit.  Returns after enqueueing.
  */
 fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
                               void *const *host_images, fbp_stream_t stream);

@@ -23,6 +23,10 @@ BpConfig bp_config(const Plan &p);
 
 using namespace fbp;
 
+// Chunks of a batch's slices that fbp_batch_run_host pipelines: while chunk c
+// computes, chunk c+1's sinograms come in and chunk c-1's images go out.
+constexpr int kRunHostChunks = 4;
+
 struct fbp_batch_s {
     int device;
     int n;
@@ -33,6 +37,15 @@ struct fbp_batch_s {
     cudaGraphExec_t exec;
     long long updates;
     int parts;
+    // fbp_batch_run_host pipeline (created on first use): a stream for the
+    // sinogram copies, one for the image copies, and the events that order
+    // them with the compute of each chunk on the caller's stream.
+    cudaStream_t s_in;
+    cudaStream_t s_out;
+    cudaEvent_t ev_start;
+    cudaEvent_t ev_out;
+    cudaEvent_t ev_in[kRunHostChunks];
+    cudaEvent_t ev_done[kRunHostChunks];
 };
 
 namespace {
@@ -42,6 +55,14 @@ void free_batch(fbp_batch_s *b)
     if (b == nullptr) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->s_in) cudaStreamDestroy(b->s_in);
+    if (b->s_out) cudaStreamDestroy(b->s_out);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    for (int c = 0; c < kRunHostChunks; ++c) {
+        if (b->ev_in[c]) cudaEventDestroy(b->ev_in[c]);
+        if (b->ev_done[c]) cudaEventDestroy(b->ev_done[c]);
+    }
     cudaFree(b->d_status);
     delete b;
 }
@@ -318,31 +339,65 @@ fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
         return FBP_ERR_INVALID_ARG;
     }
     for (int i = 0; i < b->n; ++i) {
-        const Plan &p = *b->plans[(size_t)i];
-        const fbp_batch_io &io = b->io[(size_t)i];
         if (host_sinos[i] == nullptr || host_images[i] == nullptr) {
             set_error("fbp_batch_run_host: slice %d: NULL host buffer", i);
             return FBP_ERR_INVALID_ARG;
         }
-        cudaError_t e = cudaMemcpy2DAsync(const_cast<void *>(io.sino), sizeof(float) * io.ld_sino,
-                                          host_sinos[i], sizeof(float) * p.D, sizeof(float) * p.D,
-                                          p.A, cudaMemcpyHostToDevice, stream);
+    }
+    cudaError_t e = cudaSuccess;
+    if (b->s_in == nullptr) {
+        e = cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+        for (int c = 0; c < kRunHostChunks && e == cudaSuccess; ++c) {
+            e = cudaEventCreateWithFlags(&b->ev_in[c], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done[c], cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) {
-            set_error("fbp_batch_run_host: sinogram copy: %s", cudaGetErrorString(e));
+            set_error("fbp_batch_run_host: stream/event setup: %s", cudaGetErrorString(e));
             return FBP_ERR_CUDA;
         }
     }
-    fbp_status st = fbp_batch_launch(batch, stream);
-    if (st != FBP_OK) return st;
-    for (int i = 0; i < b->n; ++i) {
-        const Plan &p = *b->plans[(size_t)i];
-        cudaError_t e = cudaMemcpyAsync(host_images[i], b->io[(size_t)i].image,
-                                        sizeof(float) * (size_t)p.n * (size_t)p.n,
-                                        cudaMemcpyDeviceToHost, stream);
-        if (e != cudaSuccess) {
-            set_error("fbp_batch_run_host: image copy: %s", cudaGetErrorString(e));
-            return FBP_ERR_CUDA;
+    const int chunks = b->n >= 4 * kRunHostChunks ? kRunHostChunks : (b->n >= 4 ? 2 : 1);
+    // The copies of this call start after everything already on `stream`
+    // (the previous call's compute still reads these device buffers).
+    e = cudaEventRecord(b->ev_start, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_in, b->ev_start, 0);
+    for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
+        const int lo = (int)((long long)b->n * c / chunks);
+        const int hi = (int)((long long)b->n * (c + 1) / chunks);
+        for (int i = lo; i < hi && e == cudaSuccess; ++i) {
+            const Plan &p = *b->plans[(size_t)i];
+            const fbp_batch_io &io = b->io[(size_t)i];
+            const size_t row = sizeof(float) * (size_t)p.D;
+            if (io.ld_sino == p.D)
+                e = cudaMemcpyAsync(const_cast<void *>(io.sino), host_sinos[i], row * (size_t)p.A,
+                                    cudaMemcpyHostToDevice, b->s_in);
+            else
+                e = cudaMemcpy2DAsync(const_cast<void *>(io.sino), sizeof(float) * io.ld_sino,
+                                      host_sinos[i], row, row, p.A, cudaMemcpyHostToDevice, b->s_in);
         }
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_in[c], b->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->ev_in[c], 0);
+        if (e == cudaSuccess)
+            e = enqueue_many(b->plans.data() + lo, b->io.data() + lo, hi - lo, b->parts,
+                             b->d_status, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_done[c], stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_out, b->ev_done[c], 0);
+        for (int i = lo; i < hi && e == cudaSuccess; ++i) {
+            const Plan &p = *b->plans[(size_t)i];
+            e = cudaMemcpyAsync(host_images[i], b->io[(size_t)i].image,
+                                sizeof(float) * (size_t)p.n * (size_t)p.n, cudaMemcpyDeviceToHost,
+                                b->s_out);
+        }
+    }
+    // `stream` is done with this call once the last image copy is.
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->ev_out, 0);
+    if (e != cudaSuccess) {
+        set_error("fbp_batch_run_host: %s", cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
     }
     return FBP_OK;
 }

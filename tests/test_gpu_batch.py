@@ -182,3 +182,38 @@ def test_batch_argument_errors(fbp):
     fbp.fbp_batch_launch(h, 0)
     fbp.fbp_batch_status(h)
     fbp.fbp_batch_destroy(h)
+
+
+def test_run_host_pipeline_equals_device_batch(fbp):
+    """fbp_batch_run_host (four pipelined chunks: sinograms in on one stream,
+    compute on the caller's, images out on a third) gives the device batch's
+    bits; a second call with new host data returns the new images, so no copy
+    of one call overtakes the compute of the other.  One slice's device
+    sinogram has padded rows (ld_sino > n_det), which takes the 2-D copy."""
+    import torch
+    specs = small_uneven_specs(17, seed=35)
+    plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det, filter=s.filter) for s in specs]
+    sinos = [_sino(s) for s in specs]
+    padded = torch.zeros((specs[3].n_angles, specs[3].n_det + 12), device="cuda")
+    padded[:, :specs[3].n_det] = sinos[3]
+    sinos[3] = padded[:, :specs[3].n_det]
+    batch = fbp.Batch(plans, sinos)
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.status()
+    want = [im.cpu().numpy() for im in batch.images]
+    host_in = [s.cpu().contiguous().pin_memory() for s in sinos]
+    host_out = [torch.full((s.n_pix, s.n_pix), float("nan")).pin_memory() for s in specs]
+    for im in batch.images:
+        im.zero_()
+    batch.run_host(host_in, host_out)
+    torch.cuda.synchronize()
+    batch.status()
+    for w, h in zip(want, host_out):
+        assert np.array_equal(h.numpy(), w)
+    # second call, new data: every image must follow its new sinogram
+    new_in = [(2.0 * h).pin_memory() for h in host_in]
+    batch.run_host(new_in, host_out)
+    torch.cuda.synchronize()
+    for plan, s_new, h in zip(plans, new_in, host_out):
+        assert np.array_equal(h.numpy(), _alone(fbp, plan, s_new.cuda()))
