@@ -33,6 +33,15 @@ METRIC = "FBP slices/s and Gupdates/s (pixel×angle) vs plain path; serving p50/
 FP32_LANES_PER_SM = 128
 OPS_PER_UPDATE = 5  # FP32-pipe operations per pixel-angle update in the algorithmic count
 FILTER_PATHS = {"auto": 0, "tc": 1, "fft": 2, "direct": 3}
+# Shared-memory ceiling of the backprojection: every update loads one 8-byte
+# (mid, slope) pair, and a warp's 8-byte shared load moves two 128-byte
+# wavefronts, so at most 16 updates per clock per SM.
+SMEM_UPDATES_PER_CLK_SM = 16
+# DRAM bytes (read + write) of one backprojection launch, measured by ncu on
+# the launch this script times (profiles/bp_persistent_kernel_batch64_512x720x725.md),
+# keyed by (geometry, slices, tile_x, tile_y, angle_chunk); reported only when
+# the tuned launch is that one, null otherwise.
+BP_TRAFFIC = {("512x720x725", 64, 32, 32, 16): 247.419392e6 + 53.687296e6}
 ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
@@ -275,6 +284,88 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
     }
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 rate (nominal; no measured figure on this machine)
+
+
+def _timed_flushed(fn, steps, stream, flush):
+    """Time fn() `steps` times with CUDA events around each call only, writing
+    `flush` (larger than L2) before each, so every call starts with a cold L2.
+    Returns the mean ms per call."""
+    import torch
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def run_configs(fbp):
+    """Per-configuration figures beside the headline, one slice per call
+    through fbp_reconstruct (the plain path), L2 flushed before each call:
+    the plain slice (256^2, 180 angles, 363 bins, Ram-Lak, FFT length 1024),
+    the float-vs-double slice on the FP64 path (against the nominal FP64 rate),
+    and the large slice (2048^2, 2048 angles, 2899 bins) with the filter time
+    of the FFT and tensor-core routes."""
+    import torch
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+
+    def one_slice(spec, dtype=0, reps=20, **opt):
+        plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter, dtype=dtype,
+                        **opt)
+        host = synthetic.sinogram(spec)
+        sino = torch.from_numpy(host if dtype == 1 else host.astype(np.float32)).cuda()
+        img, ws = plan.empty_image(), plan.empty_workspace()
+
+        def call():
+            fbp.fbp_reconstruct(plan.handle, sino.data_ptr(), sino.stride(0), img.data_ptr(),
+                                ws.data_ptr(), sp)
+        call()
+        torch.cuda.synchronize()
+        plan.device_status()
+        ms = _timed_flushed(call, reps, stream, flush)
+        return plan, sino, ms
+
+    spec = synthetic.cfg_plain()
+    _, _, ms = one_slice(spec, fft_len=1024)
+    out["plain_256x180x363"] = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
+                                "gupdates_per_s": spec.updates / (ms / 1e3) / 1e9,
+                                "path": "fbp_reconstruct, FP32, FFT length 1024"}
+    spec = synthetic.cfg_float_double()
+    _, _, ms = one_slice(spec, dtype=1, reps=5)
+    gups = spec.updates / (ms / 1e3) / 1e9
+    fp64_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2 / OPS_PER_UPDATE / 1e9
+    out["fp64_512x720x725"] = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
+                               "gupdates_per_s": gups, "fp64_peak_gupdates_per_s": fp64_peak,
+                               "frac_of_fp64_peak": gups / fp64_peak,
+                               "peak_basis": "nominal 1.25 TFLOP/s FP64 = 0.625 T FMA/s, "
+                                             "5 FP64 ops per update"}
+    spec = synthetic.cfg_large()
+    plan, sino, ms = one_slice(spec, reps=5)
+    entry = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
+             "gupdates_per_s": spec.updates / (ms / 1e3) / 1e9, "filter_ms": {}}
+    for name, path in (("fft", 2), ("tc", 1)):
+        fp = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
+                      filter_path=path)
+        q = fp.empty_filtered()
+
+        def filt():
+            fbp.fbp_filter(fp.handle, sino.data_ptr(), sino.stride(0), q.data_ptr(), sp)
+        filt()
+        torch.cuda.synchronize()
+        entry["filter_ms"][name] = _timed_flushed(filt, 5, stream, flush)
+    out["large_2048x2048x2899"] = entry
+    return out
+
+
 def run_uneven(fbp, plan_cache=None):
     """The batched configuration: 64 uneven slices (n from {256,384,512,768},
     A from {180,360,720,1440}, D = ceil(n sqrt2)+1, seeds 1000+s) in one graph,
@@ -422,7 +513,15 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "kernel": "bp_persistent_kernel", "achieved": achieved,
                      "peak": peak_gups, "unit": "Gupdates/s", "frac": achieved / peak_gups,
-                     "traffic": None,
+                     "traffic": BP_TRAFFIC.get((f"{spec0.n_pix}x{spec0.n_angles}x{spec0.n_det}",
+                                                S, plan.tuning["tile_x"], plan.tuning["tile_y"],
+                                                plan.tuning["angle_chunk"])),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+                     "smem_ceiling": {
+                         "gupdates_per_s": SMEM_UPDATES_PER_CLK_SM * sms * sm_mhz / 1e3,
+                         "frac": achieved / (SMEM_UPDATES_PER_CLK_SM * sms * sm_mhz / 1e3),
+                         "basis": "one 8-byte pair per update; an 8-byte warp load is two "
+                                  "128-byte shared-memory wavefronts: 16 updates/clk/SM"},
                      "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x {sms} SMs x {sm_mhz:.0f} "
                                    f"MHz ({pk_kind} sm_max_mhz) / {OPS_PER_UPDATE} FP32 ops per "
                                    f"update",
@@ -447,6 +546,7 @@ def run_ours(args, rank, world, local_rank):
         line["serving"] = run_serving(fbp, args.serve_seconds)
     if world == 1 and not args.no_uneven:
         line["batched_uneven"] = run_uneven(fbp)
+        line["configs"] = run_configs(fbp)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -216,7 +216,7 @@ fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream);
  * [n_angles][n_det] float, contiguous) is copied into the batch's device
  * sinogram buffer, the slice is reconstructed, and its image is copied back to
  * host_images[i] ([n_pix][n_pix] float).  The slices are processed in up to
- * four chunks, pipelined: the sinogram copies run on one internal stream, the
+ * five chunks, pipelined: the sinogram copies run on one internal stream, the
  * image copies on another, the compute on `stream`, so that chunk c+1 comes in
  * and chunk c-1 goes out while chunk c computes.  One copy per slice and
  * direction; host buffers should be pinned for the copies to be asynchronous.

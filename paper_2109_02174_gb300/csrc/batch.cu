@@ -24,8 +24,20 @@ BpConfig bp_config(const Plan &p);
 using namespace fbp;
 
 // Chunks of a batch's slices that fbp_batch_run_host pipelines: while chunk c
-// computes, chunk c+1's sinograms come in and chunk c-1's images go out.
-constexpr int kRunHostChunks = 4;
+// computes, chunk c+1's sinograms come in and chunk c-1's images go out.  Only
+// the first chunk's copy in and the last chunk's copy out are not hidden, so
+// the chunks taper at both ends: 1/16, 3/16, 1/2, 3/16, 1/16 of the slices
+// (a sinogram copies in several times faster than it computes, so each
+// chunk's copy still hides behind the previous chunk's compute).
+constexpr int kRunHostChunks = 5;
+
+// Slice index where chunk c begins (c = 0..chunks), for n slices.
+int chunk_begin(int n, int chunks, int c)
+{
+    static const int taper[kRunHostChunks + 1] = {0, 1, 4, 12, 15, 16};  // sixteenths
+    if (chunks == kRunHostChunks) return (int)((long long)n * taper[c] / 16);
+    return (int)((long long)n * c / chunks);
+}
 
 struct fbp_batch_s {
     int device;
@@ -359,14 +371,14 @@ fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
             return FBP_ERR_CUDA;
         }
     }
-    const int chunks = b->n >= 4 * kRunHostChunks ? kRunHostChunks : (b->n >= 4 ? 2 : 1);
+    const int chunks = b->n >= 16 ? kRunHostChunks : (b->n >= 4 ? 2 : 1);
     // The copies of this call start after everything already on `stream`
     // (the previous call's compute still reads these device buffers).
     e = cudaEventRecord(b->ev_start, stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->s_in, b->ev_start, 0);
     for (int c = 0; c < chunks && e == cudaSuccess; ++c) {
-        const int lo = (int)((long long)b->n * c / chunks);
-        const int hi = (int)((long long)b->n * (c + 1) / chunks);
+        const int lo = chunk_begin(b->n, chunks, c);
+        const int hi = chunk_begin(b->n, chunks, c + 1);
         for (int i = lo; i < hi && e == cudaSuccess; ++i) {
             const Plan &p = *b->plans[(size_t)i];
             const fbp_batch_io &io = b->io[(size_t)i];

@@ -185,7 +185,7 @@ def test_batch_argument_errors(fbp):
 
 
 def test_run_host_pipeline_equals_device_batch(fbp):
-    """fbp_batch_run_host (four pipelined chunks: sinograms in on one stream,
+    """fbp_batch_run_host (five pipelined chunks: sinograms in on one stream,
     compute on the caller's, images out on a third) gives the device batch's
     bits; a second call with new host data returns the new images, so no copy
     of one call overtakes the compute of the other.  One slice's device
