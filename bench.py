@@ -46,10 +46,7 @@ ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
 def workload_spec(i: int) -> synthetic.SliceSpec:
-    base = synthetic.cfg_float_double()
-    return synthetic.SliceSpec(base.n_pix, base.n_angles, base.n_det, base.n_ellipses,
-                               seed=base.seed + 1000 * i, filter=base.filter, i0=base.i0,
-                               noise_seed=base.noise_seed + 1000 * i)
+    return synthetic.cfg_float_double_slice(i)
 
 
 WORKLOAD_NAME = ("512x512 image, 720 angles on [0,pi), 725 bins, Shepp-Logan, "
@@ -529,7 +526,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": S * e2e_steps * world / (e2e_ms / 1e3), "unit": "slices/s",
                 "h2d_bytes_per_step": S * spec0.n_angles * spec0.n_det * 4,
                 "d2h_bytes_per_step": S * spec0.n_pix ** 2 * 4},
-        "gpu_launches": (S + 1) * args.steps,
+        "gpu_launches": full.kernel_count * args.steps,
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -211,6 +211,11 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
 /* Enqueue the whole batch on `stream` (one graph launch). */
 fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream);
 
+/* Number of kernel launches one fbp_batch_launch performs (the kernel nodes of
+ * the batch's graph), written to *count.  Host-only; no device work.  The
+ * paper has no counterpart (it reconstructs one image at a time). */
+fbp_status fbp_batch_kernel_count(fbp_batch_t batch, int *count);
+
 /*
  * The batch end to end from host memory: each slice's sinogram (host,
  * [n_angles][n_det] float, contiguous) is copied into the batch's device

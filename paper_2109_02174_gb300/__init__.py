@@ -93,6 +93,7 @@ _SIGS = {
     "fbp_batch_build_parts": [ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
                               ctypes.POINTER(fbp_batch_io), _I, _P],
     "fbp_batch_launch": [_P, _P],
+    "fbp_batch_kernel_count": [_P, ctypes.POINTER(_I)],
     "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
     "fbp_autotune": [_I, _I, _I, ctypes.c_double, _I, ctypes.POINTER(fbp_options), _I,
                      ctypes.POINTER(fbp_tuning)],
@@ -243,6 +244,12 @@ def fbp_batch_status(batch: int):
     _check(load_library().fbp_batch_status(batch))
 
 
+def fbp_batch_kernel_count(batch: int) -> int:
+    n = _I()
+    _check(load_library().fbp_batch_kernel_count(batch, ctypes.byref(n)))
+    return n.value
+
+
 def fbp_batch_destroy(batch: int):
     _check(load_library().fbp_batch_destroy(batch))
 
@@ -379,6 +386,11 @@ class Batch:
 
     def status(self):
         fbp_batch_status(self.handle)
+
+    @property
+    def kernel_count(self) -> int:
+        """Kernel launches per launch() (the kernel nodes of the batch graph)."""
+        return fbp_batch_kernel_count(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

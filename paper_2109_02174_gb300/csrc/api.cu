@@ -456,27 +456,31 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess && p->filter_path == FBP_PATH_FFT) {
         const int N = p->fft_len;
-        std::vector<float2> tw((size_t)N);
+        // twiddles and spectrum stored twice over (one copy per transform of a
+        // packed pair): tw[t] = (c, c, s, s), h[f] = (H, H)
+        std::vector<float4> tw((size_t)N);
         std::vector<double> ct((size_t)N);
         for (int t = 0; t < N; ++t) {
             const double a = 2.0 * M_PI * (double)t / (double)N;
             ct[(size_t)t] = std::cos(a);
-            tw[(size_t)t] = make_float2((float)std::cos(a), (float)-std::sin(a));
+            const float c = (float)std::cos(a), sn = (float)-std::sin(a);
+            tw[(size_t)t] = make_float4(c, c, sn, sn);
         }
         // H[f] = sum_m tau h(m) e^{-2 pi i f m / N} = tau h(0) + 2 sum_{m>0} tau h(m) cos(2 pi f m / N)
-        std::vector<float> hs((size_t)N);
+        std::vector<float2> hs((size_t)N);
         for (int f = 0; f < N; ++f) {
             double acc = taps[(size_t)(n_det - 1)];
             for (int m = 1; m < n_det; ++m)
                 acc += 2.0 * taps[(size_t)(n_det - 1 + m)] * ct[(size_t)(((long)f * m) % N)];
-            hs[(size_t)f] = (float)(acc / (double)N);
+            const float hv = (float)(acc / (double)N);
+            hs[(size_t)f] = make_float2(hv, hv);
         }
-        e = cudaMalloc(&p->d_fft_tw, sizeof(float2) * (size_t)N);
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_fft_h, sizeof(float) * (size_t)N);
+        e = cudaMalloc(&p->d_fft_tw, sizeof(float4) * (size_t)N);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_fft_h, sizeof(float2) * (size_t)N);
         if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_fft_tw, tw.data(), sizeof(float2) * (size_t)N, cudaMemcpyHostToDevice);
+            e = cudaMemcpy(p->d_fft_tw, tw.data(), sizeof(float4) * (size_t)N, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_fft_h, hs.data(), sizeof(float) * (size_t)N, cudaMemcpyHostToDevice);
+            e = cudaMemcpy(p->d_fft_h, hs.data(), sizeof(float2) * (size_t)N, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && p->filter_path == FBP_PATH_TOEPLITZ_TC) {
         p->tc = new TcTables();

@@ -414,6 +414,31 @@ fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
     return FBP_OK;
 }
 
+fbp_status fbp_batch_kernel_count(fbp_batch_t batch, int *count)
+{
+    fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
+    if (b == nullptr || count == nullptr) {
+        set_error("fbp_batch_kernel_count: NULL argument");
+        return FBP_ERR_INVALID_ARG;
+    }
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(b->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n > 0) e = cudaGraphGetNodes(b->graph, nodes.data(), &n);
+    int kernels = 0;
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    if (e != cudaSuccess) {
+        set_error("fbp_batch_kernel_count: %s", cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
+    }
+    *count = kernels;
+    return FBP_OK;
+}
+
 fbp_status fbp_batch_status(fbp_batch_t batch)
 {
     fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);

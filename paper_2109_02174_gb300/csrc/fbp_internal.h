@@ -41,8 +41,8 @@ struct Plan {
     double2 *d_trig64;  // (cos th_i, sin th_i) / tau
     float *d_taps32;    // tau * h(m), m = -(D-1) .. D-1
     double *d_taps64;   // same in FP64
-    float2 *d_fft_tw;   // FFT route: exp(-2 pi i t / N), t < N
-    float *d_fft_h;     // FFT route: DFT_N of the circular taps, times 1/N (real, even)
+    float4 *d_fft_tw;   // FFT route: (c, c, s, s) with c + i s = exp(-2 pi i t / N), t < N
+    float2 *d_fft_h;    // FFT route: (H, H), H = DFT_N of the circular taps / N (real, even)
     int *d_status;      // device status word (0 = ok)
     TcTables *tc;       // Toeplitz route: T_hi / T_lo and their TMA maps
 };

@@ -7,21 +7,25 @@
 // taps are symmetric), so two real rows can share one complex transform:
 // z = P_i + i P_{i+1} gives IDFT(DFT(z) . H) = Q_i + i Q_{i+1} exactly.
 //
-// One CTA of N/16 threads per row pair.  The transform is a Stockham autosort
-// FFT whose butterflies run in registers: thread t always holds 16 elements,
-// those at positions t + q N/16 (q = 0..15).  log2 N = 4a + b is done as a
-// radix-16 passes and, when b > 0, one last radix-2^b pass; between passes the
-// elements go through shared memory once (index padded by one slot per 16,
-// which keeps every pass's stores and loads free of bank conflicts).  The last
-// pass of a Stockham transform leaves each thread's results at the same
-// positions it read, so the product with H and the first pass of the inverse
-// follow in registers, without a shared-memory exchange.  Twiddles
-// exp(-2 pi i t / N) come from a plan table computed in FP64: a radix-16 pass
-// loads w^k, w^2k, w^4k, w^8k and forms the other eleven powers with at most
-// three complex products.  The 1/N of the inverse is folded into H.
-// One launch covers the row pairs of many slices with the same N (their plans
-// may differ otherwise), so a batch fills the GPU instead of running slice
-// after slice.
+// One CTA of N/16 threads per block of four rows: two complex transforms
+// (rows i, i+1 and rows i+2, i+3) computed in lockstep with packed f32x2
+// arithmetic, lane .x of every register pair belonging to the first transform
+// and lane .y to the second, so each complex add is one packed instruction
+// and each product two.  The transform is a Stockham autosort FFT whose
+// butterflies run in registers: thread t always holds the 16 elements at
+// positions t + q N/16 (q = 0..15).  log2 N = 4a + b is done as a radix-16
+// passes and, when b > 0, one last radix-2^b pass; between passes the elements
+// go through shared memory once (index padded by one slot per 16, which keeps
+// every pass's 16-byte stores and loads free of bank conflicts).  The last pass
+// of a Stockham transform leaves each thread's results at the positions it
+// read, so the product with H and the first pass of the inverse follow in
+// registers, without a shared-memory exchange.  Twiddles exp(-2 pi i t / N)
+// come from a plan table computed in FP64 and stored as broadcast pairs: a
+// radix-16 pass loads w^k, w^2k, w^4k, w^8k and forms the other eleven powers
+// with at most three complex products.  The 1/N of the inverse is folded into
+// H.  One launch covers the row blocks of many slices with the same N (their
+// plans may differ otherwise), so a batch fills the GPU instead of running
+// slice after slice.
 #include "fbp_internal.h"
 #include "pairs.cuh"
 
@@ -30,18 +34,64 @@
 namespace fbp {
 namespace {
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
-{
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Two complex numbers, one per transform: .x of each pair is the first
+// transform's, .y the second's.
+struct C2 {
+    float2 re, im;
+};
 
-// a times exp(-i pi/2) (forward) or exp(+i pi/2) (inverse).
-template <bool INV>
-__device__ __forceinline__ float2 rot90(float2 a)
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b with one rounding (b * -1 is exact)
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
 {
-    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pneg(float2 a) { return pmul(a, make_float2(-1.0f, -1.0f)); }
+
+__device__ __forceinline__ C2 cadd(const C2 &a, const C2 &b)
+{
+    return {padd(a.re, b.re), padd(a.im, b.im)};
+}
+__device__ __forceinline__ C2 csub(const C2 &a, const C2 &b)
+{
+    return {psub(a.re, b.re), psub(a.im, b.im)};
+}
+
+// A twiddle r + i s for both transforms, with n = -s kept beside it.
+struct Tw {
+    float2 r, s, n;
+};
+
+// a * w
+__device__ __forceinline__ C2 cmul(const C2 &a, const Tw &w)
+{
+    return {pfma(a.im, w.n, pmul(a.re, w.r)), pfma(a.re, w.s, pmul(a.im, w.r))};
+}
+
+// a * b of two twiddles
+__device__ __forceinline__ Tw tmul(const Tw &a, const Tw &b)
+{
+    Tw w;
+    w.r = pfma(a.n, b.s, pmul(a.r, b.r));  // ar br - as bs
+    w.s = pfma(a.s, b.r, pmul(a.r, b.s));  // ar bs + as br
+    w.n = pfma(a.n, b.r, pmul(a.r, b.n));  // -(ar bs + as br)
+    return w;
+}
+
+// Plan twiddle t, exp(-2 pi i t / N) (forward) or its conjugate (inverse).
+template <bool INV>
+__device__ __forceinline__ Tw tw_load(const float4 *__restrict__ tw, int t)
+{
+    const float4 v = __ldg(&tw[t]);
+    const float2 s = make_float2(v.z, v.w);
+    const float2 n = pneg(s);
+    Tw w;
+    w.r = make_float2(v.x, v.y);
+    w.s = INV ? n : s;
+    w.n = INV ? s : n;
+    return w;
 }
 
 // cos(pi e / 8) for e in [0, 16).
@@ -53,49 +103,58 @@ constexpr float kCosPi8[16] = {
 
 // a times exp(-+ 2 pi i E / 16).
 template <bool INV, int E>
-__device__ __forceinline__ float2 twiddle16(float2 a)
+__device__ __forceinline__ C2 twiddle16(const C2 &a)
 {
     static_assert(E >= 0 && E < 16, "exponent in [0, 16)");
     if constexpr (E == 0) {
         return a;
     } else if constexpr (E == 4) {
-        return rot90<INV>(a);
+        // times -i (forward) or +i (inverse)
+        return INV ? C2{pneg(a.im), a.re} : C2{a.im, pneg(a.re)};
     } else {
         constexpr float c = kCosPi8[E], s = kCosPi8[(E + 12) % 16];  // sin(x) = cos(x - pi/2)
-        return cmul(a, make_float2(c, INV ? s : -s));
+        const float2 C = make_float2(c, c), S = make_float2(s, s), NS = make_float2(-s, -s);
+        // forward w = c - i s; inverse w = c + i s
+        return INV ? C2{pfma(a.im, NS, pmul(a.re, C)), pfma(a.re, S, pmul(a.im, C))}
+                   : C2{pfma(a.im, S, pmul(a.re, C)), pfma(a.re, NS, pmul(a.im, C))};
     }
 }
 
 template <bool INV>
-__device__ __forceinline__ void dft2(float2 &a0, float2 &a1)
+__device__ __forceinline__ void dft2(C2 &a0, C2 &a1)
 {
-    const float2 b = csub(a0, a1);
+    const C2 b = csub(a0, a1);
     a0 = cadd(a0, a1);
     a1 = b;
 }
 
 // 4-point DFT, inputs and outputs in natural order.
 template <bool INV>
-__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+__device__ __forceinline__ void dft4(C2 &a0, C2 &a1, C2 &a2, C2 &a3)
 {
-    const float2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3);
-    const float2 b3 = rot90<INV>(csub(a1, a3));
+    const C2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), d = csub(a1, a3);
     a0 = cadd(b0, b2);
-    a1 = cadd(b1, b3);
     a2 = csub(b0, b2);
-    a3 = csub(b1, b3);
+    // forward: b1 - i d and b1 + i d; inverse: b1 + i d and b1 - i d
+    if (INV) {
+        a1 = {psub(b1.re, d.im), padd(b1.im, d.re)};
+        a3 = {padd(b1.re, d.im), psub(b1.im, d.re)};
+    } else {
+        a1 = {padd(b1.re, d.im), psub(b1.im, d.re)};
+        a3 = {psub(b1.re, d.im), padd(b1.im, d.re)};
+    }
 }
 
 // 8-point DFT as 2 x 4: q = q1 + 2 q2, m = m2 + 4 m1.
 template <bool INV>
-__device__ __forceinline__ void dft8(float2 (&a)[8])
+__device__ __forceinline__ void dft8(C2 (&a)[8])
 {
     dft4<INV>(a[0], a[2], a[4], a[6]);  // q1 = 0: A[0][m2] in a[2 m2]
     dft4<INV>(a[1], a[3], a[5], a[7]);  // q1 = 1: A[1][m2] in a[2 m2 + 1]
     a[3] = twiddle16<INV, 2>(a[3]);     // exp(-+ 2 pi i m2 / 8), m2 = 1..3
     a[5] = twiddle16<INV, 4>(a[5]);
     a[7] = twiddle16<INV, 6>(a[7]);
-    float2 x[8];
+    C2 x[8];
 #pragma unroll
     for (int m2 = 0; m2 < 4; ++m2) {
         x[m2] = cadd(a[2 * m2], a[2 * m2 + 1]);
@@ -107,7 +166,7 @@ __device__ __forceinline__ void dft8(float2 (&a)[8])
 
 // 16-point DFT as 4 x 4: q = q1 + 4 q2, m = m2 + 4 m1.
 template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16])
+__device__ __forceinline__ void dft16(C2 (&v)[16])
 {
 #pragma unroll
     for (int q1 = 0; q1 < 4; ++q1) dft4<INV>(v[q1], v[q1 + 4], v[q1 + 8], v[q1 + 12]);
@@ -124,7 +183,7 @@ __device__ __forceinline__ void dft16(float2 (&v)[16])
 #pragma unroll
     for (int m2 = 0; m2 < 4; ++m2) dft4<INV>(v[4 * m2], v[4 * m2 + 1], v[4 * m2 + 2], v[4 * m2 + 3]);
     // X[m2 + 4 m1] sits in v[m1 + 4 m2]: transpose
-    float2 x[16];
+    C2 x[16];
 #pragma unroll
     for (int m2 = 0; m2 < 4; ++m2)
 #pragma unroll
@@ -135,18 +194,20 @@ __device__ __forceinline__ void dft16(float2 (&v)[16])
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
-template <bool INV>
-__device__ __forceinline__ float2 tw_at(const float2 *__restrict__ tw, int i)
+__device__ __forceinline__ void put(float4 *buf, int i, const C2 &a)
 {
-    float2 w = __ldg(&tw[i]);
-    if (INV) w.y = -w.y;
-    return w;
+    buf[pad16(i)] = make_float4(a.re.x, a.re.y, a.im.x, a.im.y);
+}
+__device__ __forceinline__ C2 get(const float4 *buf, int i)
+{
+    const float4 f = buf[pad16(i)];
+    return {make_float2(f.x, f.y), make_float2(f.z, f.w)};
 }
 
 // Full N-point transform of the elements the block holds (thread t: positions
 // t + q N/16 in v[q]); on return v[q] holds output position t + q N/16.
 template <bool INV>
-__device__ void fft_regs(float2 (&v)[16], float2 *buf, const float2 *__restrict__ tw, int N,
+__device__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 *__restrict__ tw, int N,
                          int log2n)
 {
     const int t = threadIdx.x;
@@ -159,34 +220,34 @@ __device__ void fft_regs(float2 (&v)[16], float2 *buf, const float2 *__restrict_
         const int k = t & (ns - 1);
         if (ns > 1) {
             const int i1 = k << (log2n - 4 - log2ns);  // k N / (16 ns)
-            const float2 w1 = tw_at<INV>(tw, i1), w2 = tw_at<INV>(tw, 2 * i1);
-            const float2 w4 = tw_at<INV>(tw, 4 * i1), w8 = tw_at<INV>(tw, 8 * i1);
-            const float2 w3 = cmul(w1, w2);
-            const float2 w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+            const Tw w1 = tw_load<INV>(tw, i1), w2 = tw_load<INV>(tw, 2 * i1);
+            const Tw w4 = tw_load<INV>(tw, 4 * i1), w8 = tw_load<INV>(tw, 8 * i1);
+            const Tw w3 = tmul(w1, w2);
             v[1] = cmul(v[1], w1);
             v[2] = cmul(v[2], w2);
             v[3] = cmul(v[3], w3);
             v[4] = cmul(v[4], w4);
-            v[5] = cmul(v[5], w5);
-            v[6] = cmul(v[6], w6);
-            v[7] = cmul(v[7], w7);
+            v[5] = cmul(v[5], tmul(w4, w1));
+            v[6] = cmul(v[6], tmul(w4, w2));
+            v[7] = cmul(v[7], tmul(w4, w3));
             v[8] = cmul(v[8], w8);
-            v[9] = cmul(v[9], cmul(w8, w1));
-            v[10] = cmul(v[10], cmul(w8, w2));
-            v[11] = cmul(v[11], cmul(w8, w3));
-            v[12] = cmul(v[12], cmul(w8, w4));
-            v[13] = cmul(v[13], cmul(w8, w5));
-            v[14] = cmul(v[14], cmul(w8, w6));
-            v[15] = cmul(v[15], cmul(w8, w7));
+            v[9] = cmul(v[9], tmul(w8, w1));
+            v[10] = cmul(v[10], tmul(w8, w2));
+            v[11] = cmul(v[11], tmul(w8, w3));
+            const Tw w12 = tmul(w8, w4);
+            v[12] = cmul(v[12], w12);
+            v[13] = cmul(v[13], tmul(w12, w1));
+            v[14] = cmul(v[14], tmul(w12, w2));
+            v[15] = cmul(v[15], tmul(w12, w3));
         }
         dft16<INV>(v);
         if (!last) {
             const int o = ((t - k) << 4) + k;
 #pragma unroll
-            for (int m = 0; m < 16; ++m) buf[pad16(o + m * ns)] = v[m];
+            for (int m = 0; m < 16; ++m) put(buf, o + m * ns, v[m]);
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = buf[pad16(t + q * T)];
+            for (int q = 0; q < 16; ++q) v[q] = get(buf, t + q * T);
             __syncthreads();
         }
         ns <<= 4;
@@ -199,9 +260,9 @@ __device__ void fft_regs(float2 (&v)[16], float2 *buf, const float2 *__restrict_
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             const int j = t + m * T;
-            float2 a[8];
+            C2 a[8];
 #pragma unroll
-            for (int s = 0; s < 8; ++s) a[s] = s ? cmul(v[m + 2 * s], tw_at<INV>(tw, s * j)) : v[m];
+            for (int s = 0; s < 8; ++s) a[s] = s ? cmul(v[m + 2 * s], tw_load<INV>(tw, s * j)) : v[m];
             dft8<INV>(a);
 #pragma unroll
             for (int s = 0; s < 8; ++s) v[m + 2 * s] = a[s];
@@ -210,9 +271,9 @@ __device__ void fft_regs(float2 (&v)[16], float2 *buf, const float2 *__restrict_
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int j = t + m * T;
-            float2 a1 = cmul(v[m + 4], tw_at<INV>(tw, j));
-            float2 a2 = cmul(v[m + 8], tw_at<INV>(tw, 2 * j));
-            float2 a3 = cmul(v[m + 12], tw_at<INV>(tw, 3 * j));
+            C2 a1 = cmul(v[m + 4], tw_load<INV>(tw, j));
+            C2 a2 = cmul(v[m + 8], tw_load<INV>(tw, 2 * j));
+            C2 a3 = cmul(v[m + 12], tw_load<INV>(tw, 3 * j));
             dft4<INV>(v[m], a1, a2, a3);
             v[m + 4] = a1;
             v[m + 8] = a2;
@@ -222,26 +283,26 @@ __device__ void fft_regs(float2 (&v)[16], float2 *buf, const float2 *__restrict_
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int j = t + m * T;
-            float2 a1 = cmul(v[m + 8], tw_at<INV>(tw, j));
+            C2 a1 = cmul(v[m + 8], tw_load<INV>(tw, j));
             dft2<INV>(v[m], a1);
             v[m + 8] = a1;
         }
     }
 }
 
-// One slice's part of a launch; pair_end is the inclusive prefix sum of the
-// slices' row-pair counts, so CTA b works on the slice s with
-// pair_end[s-1] <= b < pair_end[s].  All slices of a launch share N.
+// One slice's part of a launch; block_end is the inclusive prefix sum of the
+// slices' four-row block counts, so CTA b works on the slice s with
+// block_end[s-1] <= b < block_end[s].  All slices of a launch share N.
 struct FftSlice {
     const float *sino;
     void *q;
-    const float2 *tw;
-    const float *h;
+    const float4 *tw;
+    const float2 *h;
     int ld;
     int pitch;
     int A;
     int D;
-    int pair_end;
+    int block_end;
     int pad_;
 };
 
@@ -256,52 +317,62 @@ struct FftLaunch {
 template <typename OutT, int MAXS>
 __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __grid_constant__ FftLaunch<MAXS> L)
 {
-    extern __shared__ float2 buf[];
+    extern __shared__ float4 buf[];
     int lo = 0, hi = L.n - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if ((int)blockIdx.x < L.s[mid].pair_end) hi = mid; else lo = mid + 1;
+        if ((int)blockIdx.x < L.s[mid].block_end) hi = mid; else lo = mid + 1;
     }
     const FftSlice &S = L.s[lo];
-    const int pair = (int)blockIdx.x - (lo > 0 ? L.s[lo - 1].pair_end : 0);
+    const int blk = (int)blockIdx.x - (lo > 0 ? L.s[lo - 1].block_end : 0);
     const int N = L.N, D = S.D, T = N >> 4, t = threadIdx.x;
-    const int i0 = 2 * pair;
-    const bool two = i0 + 1 < S.A;
+    const int i0 = 4 * blk;
+    const int rows = min(4, S.A - i0);  // 1..4 rows in this block
+    // rows i0, i0+1 -> transform 0 (re, im); rows i0+2, i0+3 -> transform 1;
+    // a row past the slice is never read
     const float *p0 = S.sino + (size_t)i0 * S.ld;
-    const float *p1 = S.sino + (size_t)(two ? i0 + 1 : i0) * S.ld;
-    float2 v[16];
+    const float *p1 = p0 + (rows > 1 ? S.ld : 0);
+    const float *p2 = p0 + (rows > 2 ? 2 * (size_t)S.ld : 0);
+    const float *p3 = p0 + (rows > 3 ? 3 * (size_t)S.ld : 0);
+    C2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const int j = t + q * T;
-        v[q] = make_float2(0.0f, 0.0f);
+        v[q].re = make_float2(0.0f, 0.0f);
+        v[q].im = make_float2(0.0f, 0.0f);
         if (j < D) {
-            v[q].x = p0[j];
-            v[q].y = two ? p1[j] : 0.0f;
+            v[q].re.x = p0[j];
+            if (rows > 1) v[q].im.x = p1[j];
+            if (rows > 2) v[q].re.y = p2[j];
+            if (rows > 3) v[q].im.y = p3[j];
         }
     }
     fft_regs<false>(v, buf, S.tw, N, L.log2n);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        const float hv = __ldg(&S.h[t + q * T]);
-        v[q] = make_float2(v[q].x * hv, v[q].y * hv);
+        const float2 hv = __ldg(&S.h[t + q * T]);
+        v[q].re = pmul(v[q].re, hv);
+        v[q].im = pmul(v[q].im, hv);
     }
     fft_regs<true>(v, buf, S.tw, N, L.log2n);
     // every thread is past its last read of buf (the final pass of the inverse
     // reads none; the one before ends with a barrier)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) buf[pad16(t + q * T)] = v[q];
+    for (int q = 0; q < 16; ++q) put(buf, t + q * T, v[q]);
     __syncthreads();
-    // buf[k] = (Q_i0[k], Q_i0+1[k]) for k < n_det; write (mid, slope) pairs.
+    // buf[k] holds Q of the four rows at bin k (k < n_det): (row 0, row 2,
+    // row 1, row 3); write (mid, slope) pairs.
     OutT *r0 = static_cast<OutT *>(S.q) + (size_t)i0 * S.pitch;
-    OutT *r1 = static_cast<OutT *>(S.q) + (size_t)(i0 + 1) * S.pitch;
     for (int p = t; p < S.pitch / 2; p += T) {
-        float2 a = make_float2(0.0f, 0.0f), b = make_float2(0.0f, 0.0f);
+        float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a;
         if (p <= D) {
             if (p >= 1) a = buf[pad16(p - 1)];
             if (p < D) b = buf[pad16(p)];
         }
         store_pair(r0, p, a.x, b.x);
-        if (two) store_pair(r1, p, a.y, b.y);
+        if (rows > 1) store_pair(r0 + S.pitch, p, a.z, b.z);
+        if (rows > 2) store_pair(r0 + 2 * (size_t)S.pitch, p, a.y, b.y);
+        if (rows > 3) store_pair(r0 + 3 * (size_t)S.pitch, p, a.w, b.w);
     }
 }
 
@@ -336,23 +407,23 @@ FftSlice fft_slice(const Plan &p, const float *sino, int ld, void *q)
     f.pitch = p.pitch;
     f.A = p.A;
     f.D = p.D;
-    f.pair_end = 0;
+    f.block_end = 0;
     f.pad_ = 0;
     return f;
 }
 
 }  // namespace
 
-size_t filter_fft_smem_bytes(int N) { return sizeof(float2) * (size_t)(N + N / 16); }
+size_t filter_fft_smem_bytes(int N) { return sizeof(float4) * (size_t)(N + N / 16); }
 
 cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q, cudaStream_t s)
 {
     FftLaunch<1> L;
     L.s[0] = fft_slice(p, sino, ld, q);
-    L.s[0].pair_end = (p.A + 1) / 2;
+    L.s[0].block_end = (p.A + 3) / 4;
     L.n = 1;
-    if (p.q_storage == FBP_F16) return launch_set<__half, 1>(L, L.s[0].pair_end, p.fft_len, s);
-    return launch_set<float, 1>(L, L.s[0].pair_end, p.fft_len, s);
+    if (p.q_storage == FBP_F16) return launch_set<__half, 1>(L, L.s[0].block_end, p.fft_len, s);
+    return launch_set<float, 1>(L, L.s[0].block_end, p.fft_len, s);
 }
 
 cudaError_t launch_filter_fft_many(const Plan *const *plans, const float *const *sinos,
@@ -386,8 +457,8 @@ cudaError_t launch_filter_fft_many(const Plan *const *plans, const float *const 
                     (p.q_storage == FBP_F16) != (half == 1))
                     continue;
                 L.s[cnt] = fft_slice(p, sinos[i], lds[i], qs[i]);
-                total += (p.A + 1) / 2;
-                L.s[cnt].pair_end = total;
+                total += (p.A + 3) / 4;
+                L.s[cnt].block_end = total;
                 if (++cnt == kFftMaxSlices) {
                     cudaError_t e = flush();
                     if (e != cudaSuccess) return e;

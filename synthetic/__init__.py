@@ -179,6 +179,16 @@ def cfg_float_double() -> SliceSpec:
     return SliceSpec(512, 720, 725, 20, seed=2, filter=1, i0=1e5, noise_seed=102)
 
 
+def cfg_float_double_slice(i: int) -> SliceSpec:
+    """Slice i of a batch of float-vs-double slices: the same geometry and
+    recipe, phantom seed 2 + 1000 i and noise seed 102 + 1000 i (i = 0 is
+    cfg_float_double itself)."""
+    base = cfg_float_double()
+    return SliceSpec(base.n_pix, base.n_angles, base.n_det, base.n_ellipses,
+                     seed=base.seed + 1000 * i, filter=base.filter, i0=base.i0,
+                     noise_seed=base.noise_seed + 1000 * i)
+
+
 def cfg_large() -> SliceSpec:
     """2048x2048, 2048 angles, 2899 bins, Ram-Lak, 40 ellipses, seed 4."""
     return SliceSpec(2048, 2048, 2899, 40, seed=4, filter=0)

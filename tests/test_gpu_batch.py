@@ -217,3 +217,14 @@ def test_run_host_pipeline_equals_device_batch(fbp):
     torch.cuda.synchronize()
     for plan, s_new, h in zip(plans, new_in, host_out):
         assert np.array_equal(h.numpy(), _alone(fbp, plan, s_new.cuda()))
+
+
+def test_kernel_count_of_a_same_plan_batch(fbp):
+    """Four slices of one FFT-route plan: one filter launch over all row pairs
+    and one backprojection launch over all tiles (two slices per item)."""
+    n, A = 96, 60
+    D = synthetic.det_for(n)
+    plan = fbp.Plan(n, A, D, filter_path=2)
+    sinos = [_sino(synthetic.SliceSpec(n, A, D, 4, seed=990 + i)) for i in range(4)]
+    batch = fbp.Batch([plan] * 4, sinos)
+    assert batch.kernel_count == 2
