@@ -41,7 +41,7 @@ SMEM_UPDATES_PER_CLK_SM = 16
 # the launch this script times (profiles/bp_persistent_kernel_batch64_512x720x725.md),
 # keyed by (geometry, slices, tile_x, tile_y, angle_chunk); reported only when
 # the tuned launch is that one, null otherwise.
-BP_TRAFFIC = {("512x720x725", 64, 32, 32, 16): 247.419392e6 + 53.687296e6}
+BP_TRAFFIC = {("512x720x725", 64, 32, 32, 32): 255.6288e6 + 56.35712e6}
 ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
@@ -418,9 +418,13 @@ def run_ours(args, rank, world, local_rank):
     host = [synthetic.sinogram(s, theta).astype(np.float32) for s in specs]
     # the autotuner picks the filter route and backprojection shape for this
     # geometry on this GPU (timed over a batch; cached in FBP_TUNE_CACHE if set)
+    shape = {}
+    if args.tile:
+        tx, ty = (int(v) for v in args.tile.split("x"))
+        shape = {"tile_x": tx, "tile_y": ty, "angle_chunk": args.chunk}
     plan = fbp.Plan(spec0.n_pix, spec0.n_angles, spec0.n_det, filter=spec0.filter,
                     autotune=True, batch_hint=min(S, 64),
-                    filter_path=FILTER_PATHS[args.filter_path])
+                    filter_path=FILTER_PATHS[args.filter_path], **shape)
     sinos = [torch.from_numpy(h).to(dev) for h in host]
     works = [plan.empty_workspace() for _ in range(S)]
     images = [plan.empty_image() for _ in range(S)]
@@ -560,6 +564,10 @@ def main():
                     help="skip the 64-uneven-slice batch measurement")
     ap.add_argument("--filter-path", choices=sorted(FILTER_PATHS), default="auto",
                     help="ramp-filter route (auto: the autotuner picks)")
+    ap.add_argument("--tile", default="",
+                    help="backprojection tile WxH (32x64, 32x32, 8x32) instead of the tuned one")
+    ap.add_argument("--chunk", type=int, default=16, choices=(8, 16, 32),
+                    help="angles per shared-memory stage with --tile")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson serving run (0 = skip)")
     args = ap.parse_args()

@@ -310,8 +310,8 @@ typedef struct {
 
 /* Tune the geometry (allocates test buffers for `batch` (1..64) slices while it
  * runs; synchronises the device).  base may be NULL (defaults); FP32 only.  A
- * filter_path other than FBP_PATH_AUTO in base is kept, and only the
- * backprojection shape is tuned for it. */
+ * filter_path other than FBP_PATH_AUTO, a tile (tile_x, tile_y) or an
+ * angle_chunk set in base is kept, and only the rest is tuned. */
 fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
                         fbp_filter_type filter, const fbp_options *base, int batch,
                         fbp_tuning *out);

@@ -1,7 +1,8 @@
 // Autotuner: picks, per geometry ("shape bucket"), the filter route and the
 // backprojection launch shape (pixel tile, angles per shared-memory stage) by
-// timing them on the device, and caches the choice per GPU model.  A route
-// fixed in the base options is kept (only the shape is tuned then).
+// timing them on the device, and caches the choice per GPU model.  A route,
+// tile or angle chunk fixed in the base options is kept (only the rest is
+// tuned then).
 //
 // The two kernels are independent, so they are tuned separately: every
 // available filter route (FFT, tensor-core Toeplitz, direct) on `batch` slices,
@@ -51,8 +52,9 @@ std::string bucket_key(int n, int A, int D, double tau, int filter, const fbp_op
                        int batch)
 {
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%.9g|%d|%d|%d|%d|%d|%d", gpu_name().c_str(), n, A, D,
-             tau, filter, b.dtype, b.q_storage, b.accumulate, b.filter_path, batch);
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%.9g|%d|%d|%d|%d|%d|%dx%dx%d|%d", gpu_name().c_str(), n,
+             A, D, tau, filter, b.dtype, b.q_storage, b.accumulate, b.filter_path, b.tile_x,
+             b.tile_y, b.angle_chunk, batch);
     return buf;
 }
 
@@ -207,7 +209,9 @@ fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
     const int tiles[3][2] = {{32, 64}, {32, 32}, {8, 32}};
     const int chunks[3] = {8, 16, 32};
     for (int ti = 0; ti < 3; ++ti) {
+        if (b.tile_x > 0 && (b.tile_x != tiles[ti][0] || b.tile_y != tiles[ti][1])) continue;
         for (int ci = 0; ci < 3; ++ci) {
+            if (b.angle_chunk > 0 && b.angle_chunk != chunks[ci]) continue;
             fbp_options o = b;
             o.filter_path = best.options.filter_path ? best.options.filter_path : FBP_PATH_AUTO;
             o.tile_x = tiles[ti][0];
