@@ -308,7 +308,8 @@ def run_configs(fbp):
     the plain slice (256^2, 180 angles, 363 bins, Ram-Lak, FFT length 1024),
     the float-vs-double slice on the FP64 path (against the nominal FP64 rate),
     and the large slice (2048^2, 2048 angles, 2899 bins) with the filter time
-    of the FFT and tensor-core routes."""
+    of the FFT and tensor-core routes and the speed of its FP16-pair and Kahan
+    variants."""
     import torch
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
@@ -359,6 +360,10 @@ def run_configs(fbp):
         filt()
         torch.cuda.synchronize()
         entry["filter_ms"][name] = _timed_flushed(filt, 5, stream, flush)
+    entry["variants_gupdates_per_s"] = {}
+    for name, opt in (("fp16_pairs", {"q_storage": 2}), ("kahan", {"accumulate": 1})):
+        _, _, vms = one_slice(spec, reps=5, **opt)
+        entry["variants_gupdates_per_s"][name] = spec.updates / (vms / 1e3) / 1e9
     out["large_2048x2048x2899"] = entry
     return out
 

@@ -84,3 +84,20 @@ def test_tuning_cache_file_survives_processes(fbp, tmp_path):
                       .strip().splitlines()[-1])
     assert out2["from_cache"] == 1
     assert out2["tile_x"] == out1["tile_x"] and out2["filter_path"] == out1["filter_path"]
+
+
+def test_autotune_keeps_fixed_route_tile_and_chunk(fbp):
+    """A filter route, tile or angle chunk given in the base options is kept;
+    only the rest is tuned (and cached under its own key)."""
+    n, A = 128, 180
+    D = synthetic.det_for(n)
+    base = fbp.fbp_options_default()
+    base.filter_path = fbp.FBP_PATH_FFT
+    base.tile_x, base.tile_y = 8, 32
+    t = fbp.fbp_autotune(n, A, D, base=base, batch=2)
+    assert t["filter_path"] == fbp.FBP_PATH_FFT
+    assert (t["tile_x"], t["tile_y"]) == (8, 32)
+    assert t["angle_chunk"] in (8, 16, 32)
+    base.angle_chunk = 32
+    t2 = fbp.fbp_autotune(n, A, D, base=base, batch=2)
+    assert (t2["tile_x"], t2["tile_y"], t2["angle_chunk"]) == (8, 32, 32)
