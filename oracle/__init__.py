@@ -75,6 +75,8 @@ def _load():
             lib.oracle_forward.restype = None
             lib.oracle_fbp.argtypes = [d, i, i, i, d, ctypes.c_double, i, i, d, i]
             lib.oracle_fbp.restype = i
+            lib.oracle_lambert_beer.argtypes = [d, ctypes.c_long, ctypes.c_double, d]
+            lib.oracle_lambert_beer.restype = None
             _lib = lib
     return _lib
 
@@ -94,6 +96,15 @@ def _f64(a) -> np.ndarray:
 def default_angles(n_angles: int) -> np.ndarray:
     """theta_i = i*pi/n_angles, i = 0..n_angles-1 (uniform on [0, pi))."""
     return np.arange(n_angles, dtype=np.float64) * (np.pi / n_angles)
+
+
+def lambert_beer(I, i0: float) -> np.ndarray:
+    """Eq. 1: line integrals p = -ln(max(I, 1) / i0) of measured intensities or
+    photon counts I (any shape)."""
+    I = _f64(I)
+    p = np.empty_like(I)
+    _load().oracle_lambert_beer(_dp(I), int(I.size), float(i0), _dp(p))
+    return p
 
 
 def taps(kind: int, n_det: int, tau: float = 1.0) -> np.ndarray:

@@ -35,6 +35,20 @@
 enum { ORACLE_RAM_LAK = 0, ORACLE_SHEPP_LOGAN = 1, ORACLE_NONE = 2 };
 
 /*
+ * Lambert-Beer (Eq. 1): a ray of incident intensity i0 leaves the object with
+ * I = i0 exp(-integral of mu), so the line integral the filter takes is
+ * p = -ln(I / i0).  A measured count of zero has no logarithm; one count is
+ * the floor (p = -ln(max(I, 1) / i0)).  n values, in order.
+ */
+void oracle_lambert_beer(const double *I, long n, double i0, double *p)
+{
+    for (long k = 0; k < n; ++k) {
+        const double v = I[k] > 1.0 ? I[k] : 1.0;
+        p[k] = -log(v / i0);
+    }
+}
+
+/*
  * Spatial filter taps H (the convolution kernel of Q = P * H, text after
  * Eq. 2).  The paper does not name H; the band-limited ramp kernels of
  * Kak & Slaney ("Principles of Computerized Tomographic Imaging", ch. 3) are

@@ -115,11 +115,16 @@ def analytic_projection(ellipses, theta: np.ndarray, n_det: int, n_pix: int,
     return p
 
 
+def poisson_counts(p_phantom: np.ndarray, i0: float, noise_seed: int) -> np.ndarray:
+    """Lambert-Beer (Eq. 1) measurement: photon counts ~ Poisson(i0 e^-p), float64."""
+    rng = np.random.Generator(np.random.PCG64(noise_seed))
+    return rng.poisson(i0 * np.exp(-p_phantom)).astype(np.float64)
+
+
 def poisson_log(p_phantom: np.ndarray, i0: float, noise_seed: int) -> np.ndarray:
     """Lambert-Beer (Eq. 1) measurement and its log transform, float64."""
-    rng = np.random.Generator(np.random.PCG64(noise_seed))
-    counts = rng.poisson(i0 * np.exp(-p_phantom))
-    return -np.log(np.maximum(counts, 1).astype(np.float64) / i0)
+    counts = poisson_counts(p_phantom, i0, noise_seed)
+    return -np.log(np.maximum(counts, 1.0) / i0)
 
 
 def phantom_image(ellipses, n_pix: int, supersample: int = 4) -> np.ndarray:
@@ -166,6 +171,19 @@ def sinogram(spec: SliceSpec, theta: np.ndarray | None = None) -> np.ndarray:
     if spec.i0 is not None:
         p = poisson_log(p, spec.i0, spec.noise_seed if spec.noise_seed is not None else spec.seed)
     return p * (0.5 * spec.n_pix)
+
+
+def photon_counts(spec: SliceSpec, theta: np.ndarray | None = None) -> np.ndarray:
+    """The raw measurement behind a noisy slice: photon counts [n_angles][n_det]
+    (float64) for the analytic projections in phantom units, the same draw
+    sinogram() log-transforms.  Requires spec.i0."""
+    if spec.i0 is None:
+        raise ValueError("photon_counts needs a noisy spec (i0 set)")
+    if theta is None:
+        theta = default_angles(spec.n_angles)
+    ell = random_ellipses(spec.n_ellipses, spec.seed)
+    p = analytic_projection(ell, theta, spec.n_det, spec.n_pix, spec.tau)
+    return poisson_counts(p, spec.i0, spec.noise_seed if spec.noise_seed is not None else spec.seed)
 
 
 # Workloads: the five configurations of the benchmark plan, as synthetic recipes.

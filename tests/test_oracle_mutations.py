@@ -28,6 +28,9 @@ MUTATIONS = [
      "double u = t / tau + 0.5 * (double)n_det;\n        s += interp"),
     ("splat weights swapped", "if (k >= 0 && k < n_det) p[k] += (1.0 - w) * v;",
      "if (k >= 0 && k < n_det) p[k] += w * v;"),
+    ("Lambert-Beer without the one-count floor", "const double v = I[k] > 1.0 ? I[k] : 1.0;",
+     "const double v = I[k];"),
+    ("Lambert-Beer sign", "p[k] = -log(v / i0);", "p[k] = log(v / i0);"),
 ]
 
 

@@ -264,3 +264,19 @@ def test_threaded_filter_and_fbp_match_single_thread():
     th = oracle.default_angles(13)
     np.testing.assert_array_equal(oracle.fbp(P, th, 1.0, oracle.SHEPP_LOGAN, 21, nthreads=5),
                                   oracle.fbp(P, th, 1.0, oracle.SHEPP_LOGAN, 21, nthreads=1))
+
+
+def test_lambert_beer_round_trip_and_floor():
+    """Eq. 1: intensities made as I = i0 e^-p give back p (to rounding); counts
+    at or below one photon give the floor ln(i0); scaling I and i0 together
+    leaves p unchanged (above the floor)."""
+    p = np.linspace(0.0, 9.0, 37)
+    i0 = 1e5
+    got = oracle.lambert_beer(i0 * np.exp(-p), i0)
+    assert np.allclose(got, p, rtol=0, atol=1e-12)
+    floor = oracle.lambert_beer(np.array([0.0, 0.5, 1.0, -3.0]), i0)
+    assert np.allclose(floor, math.log(i0), rtol=0, atol=1e-12)
+    counts = np.array([[2.0, 17.0, 4096.0], [99999.0, 3.0, 1.5]])
+    assert np.allclose(oracle.lambert_beer(8.0 * counts, 8.0 * i0),
+                       oracle.lambert_beer(counts, i0), rtol=0, atol=1e-12)
+    assert oracle.lambert_beer(counts, i0).shape == counts.shape
