@@ -309,7 +309,8 @@ def run_configs(fbp):
     the float-vs-double slice on the FP64 path (against the nominal FP64 rate),
     and the large slice (2048^2, 2048 angles, 2899 bins) with the filter time
     of the FFT and tensor-core routes and the speed of its FP16-pair and Kahan
-    variants."""
+    variants; and the batched filter of 64 float-vs-double slices fed line
+    integrals or photon counts (Lambert-Beer conversion on load)."""
     import torch
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
@@ -360,6 +361,19 @@ def run_configs(fbp):
         filt()
         torch.cuda.synchronize()
         entry["filter_ms"][name] = _timed_flushed(filt, 5, stream, flush)
+    # the Lambert-Beer conversion fused into the filter's loads: the batched
+    # filter of 64 float-vs-double slices from line integrals and from counts
+    fb = synthetic.cfg_float_double()
+    lb = {}
+    for name, i0 in (("line_integrals", 0.0), ("photon_counts", fb.i0)):
+        fp = fbp.Plan(fb.n_pix, fb.n_angles, fb.n_det, filter=fb.filter, filter_path=2, i0=i0)
+        src = [torch.full((fb.n_angles, fb.n_det), 5000.0, device="cuda") for _ in range(64)]
+        fbatch = fbp.Batch([fp] * 64, src, parts=fbp.FBP_BATCH_FILTER)
+        fbatch.launch()
+        torch.cuda.synchronize()
+        lb[name] = _timed_flushed(fbatch.launch, 5, stream, flush) / 64 * 1e3
+        fbatch.close()
+    out["lambert_beer_on_load_us_per_slice"] = lb
     entry["variants_gupdates_per_s"] = {}
     for name, opt in (("fp16_pairs", {"q_storage": 2}), ("kahan", {"accumulate": 1})):
         _, _, vms = one_slice(spec, reps=5, **opt)
@@ -552,6 +566,7 @@ def run_ours(args, rank, world, local_rank):
         line["serving"] = run_serving(fbp, args.serve_seconds)
     if world == 1 and not args.no_uneven:
         line["batched_uneven"] = run_uneven(fbp)
+    if world == 1 and not args.no_configs:
         line["configs"] = run_configs(fbp)
     print(json.dumps(line), flush=True)
     return 0
@@ -567,6 +582,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the 64-uneven-slice batch measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-configuration measurements")
     ap.add_argument("--filter-path", choices=sorted(FILTER_PATHS), default="auto",
                     help="ramp-filter route (auto: the autotuner picks)")
     ap.add_argument("--tile", default="",

@@ -86,6 +86,11 @@ typedef struct {
     int tile_x;       /* 0 = auto; pixel tile of one backprojection work item */
     int tile_y;       /* 0 = auto */
     int angle_chunk;  /* 0 = auto; angles staged per shared-memory window */
+    double i0;        /* 0 (default): the sinogram holds line integrals p.  > 0: it
+                         holds measured intensities or photon counts I of rays with
+                         incident intensity i0, and every filter route converts them
+                         as it loads them, p = -ln(max(I, 1) / i0) (Eq. 1,
+                         Lambert-Beer; one count is the floor).  Must be finite. */
 } fbp_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -61,7 +61,7 @@ class fbp_server_stats(ctypes.Structure):
 class fbp_options(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in
                 ("dtype", "q_storage", "accumulate", "filter_path", "fft_len",
-                 "tile_x", "tile_y", "angle_chunk")]
+                 "tile_x", "tile_y", "angle_chunk")] + [("i0", ctypes.c_double)]
 
 
 class fbp_tuning(ctypes.Structure):
@@ -276,7 +276,7 @@ class Plan:
                  autotune: bool = False, batch_hint: int = 8, **options):
         opt = fbp_options_default()
         for k, v in options.items():
-            setattr(opt, k, int(v))
+            setattr(opt, k, float(v) if k == "i0" else int(v))
         self.tuning = None
         if autotune:
             self.tuning = fbp_autotune(n_pix, n_angles, n_det, det_spacing, filter, opt,

@@ -320,6 +320,10 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         set_error("fbp_plan: dtype %d not built", o.dtype);
         return FBP_ERR_UNSUPPORTED;
     }
+    if (!std::isfinite(o.i0) || o.i0 < 0.0) {
+        set_error("fbp_plan: i0 must be 0 (line integrals) or a positive incident intensity");
+        return FBP_ERR_INVALID_ARG;
+    }
     if (o.dtype == FBP_F64) {
         // The FP64 path is the direct filter and a plain per-pixel backprojection.
         if (o.q_storage != FBP_F32 || o.accumulate != FBP_ACC_PLAIN ||
@@ -393,6 +397,9 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     p->filter_path = path;
     p->fft_len = (path == FBP_PATH_FFT) ? fft_len : 0;
     p->tau = det_spacing;
+    p->i0 = o.i0;
+    p->i0f = (float)o.i0;
+    p->ln_i0f = o.i0 > 0.0 ? (float)std::log(o.i0) : 0.0f;
     p->scale64 = M_PI / (double)n_angles;
     p->scale32 = (float)p->scale64;
     if (cudaGetDevice(&p->device) != cudaSuccess) {

@@ -35,6 +35,9 @@ struct Plan {
     int bp_wy;
     int bp_wp;
     int bp_chunk;  // angles per shared-memory stage (8, 16, 32)
+    double i0;       // > 0: the sinogram holds intensities, converted on load (Eq. 1)
+    float i0f;
+    float ln_i0f;    // ln(i0) (FP64, rounded)
     float scale32;   // pi / A
     double scale64;  // pi / A
     // Device tables owned by the plan.

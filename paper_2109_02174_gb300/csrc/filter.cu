@@ -3,8 +3,9 @@
 // One CTA per sinogram row; the row and the 2*n_det-1 taps sit in shared
 // memory; each thread owns output bins k, k + blockDim, ... and sums j in
 // increasing order (deterministic).  The row is then written as (mid, slope)
-// pairs (pairs.cuh).
+// pairs (pairs.cuh).  Intensity input is converted on load (lambert.cuh).
 #include "fbp_internal.h"
+#include "lambert.cuh"
 #include "pairs.cuh"
 
 namespace fbp {
@@ -13,7 +14,7 @@ namespace {
 template <typename OutT>
 __global__ void __launch_bounds__(256)
     filter_direct_kernel(const float *__restrict__ sino, int ld, const float *__restrict__ taps,
-                         OutT *__restrict__ q, int D, int pitch)
+                         OutT *__restrict__ q, int D, int pitch, float i0, float ln_i0)
 {
     extern __shared__ float sm[];
     float *st = sm;                // taps, index m + D - 1
@@ -21,7 +22,8 @@ __global__ void __launch_bounds__(256)
     float *sq = sp + D;            // sq[k + 1] = Q[k], sq[0] = sq[D + 1] = 0
     const int i = blockIdx.x;
     for (int t = threadIdx.x; t < 2 * D - 1; t += blockDim.x) st[t] = taps[t];
-    for (int t = threadIdx.x; t < D; t += blockDim.x) sp[t] = sino[(size_t)i * ld + t];
+    for (int t = threadIdx.x; t < D; t += blockDim.x)
+        sp[t] = line_integral(sino[(size_t)i * ld + t], i0, ln_i0);
     if (threadIdx.x == 0) {
         sq[0] = 0.0f;
         sq[D + 1] = 0.0f;
@@ -50,7 +52,8 @@ cudaError_t launch(const Plan &p, const float *sino, int ld, OutT *q, cudaStream
     cudaError_t e = cudaFuncSetAttribute(filter_direct_kernel<OutT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    filter_direct_kernel<OutT><<<p.A, 256, smem, s>>>(sino, ld, p.d_taps32, q, p.D, p.pitch);
+    filter_direct_kernel<OutT><<<p.A, 256, smem, s>>>(sino, ld, p.d_taps32, q, p.D, p.pitch,
+                                                       p.i0f, p.ln_i0f);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@
 // plans may differ otherwise), so a batch fills the GPU instead of running
 // slice after slice.
 #include "fbp_internal.h"
+#include "lambert.cuh"
 #include "pairs.cuh"
 
 #include <vector>
@@ -303,6 +304,8 @@ struct FftSlice {
     int A;
     int D;
     int block_end;
+    float i0;  // > 0: intensity input, converted on load (lambert.cuh)
+    float ln_i0;
     int pad_;
 };
 
@@ -345,6 +348,18 @@ __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __gri
             if (rows > 1) v[q].im.x = p1[j];
             if (rows > 2) v[q].re.y = p2[j];
             if (rows > 3) v[q].im.y = p3[j];
+        }
+    }
+    if (S.i0 > 0.0f) {
+        // intensities: convert after all loads are in flight (the padding stays zero)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (t + q * T < D) {
+                v[q].re.x = line_integral(v[q].re.x, S.i0, S.ln_i0);
+                if (rows > 1) v[q].im.x = line_integral(v[q].im.x, S.i0, S.ln_i0);
+                if (rows > 2) v[q].re.y = line_integral(v[q].re.y, S.i0, S.ln_i0);
+                if (rows > 3) v[q].im.y = line_integral(v[q].im.y, S.i0, S.ln_i0);
+            }
         }
     }
     fft_regs<false>(v, buf, S.tw, N, L.log2n);
@@ -408,6 +423,8 @@ FftSlice fft_slice(const Plan &p, const float *sino, int ld, void *q)
     f.A = p.A;
     f.D = p.D;
     f.block_end = 0;
+    f.i0 = p.i0f;
+    f.ln_i0 = p.ln_i0f;
     f.pad_ = 0;
     return f;
 }

@@ -31,6 +31,7 @@
 // tensor memory and exits.
 #include "fbp_internal.h"
 #include "filter_tc.cuh"
+#include "lambert.cuh"
 #include "ptx.cuh"
 
 #include <cstring>
@@ -176,6 +177,8 @@ struct TcArgs {
     int pitch;
     int nk;       // K chunks
     int m_tiles;  // row tiles per slice
+    float i0;     // > 0: intensity input, converted on load
+    float ln_i0;
     int *status;
 };
 
@@ -343,8 +346,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < kRowsPerLoader; ++i) {
                 const int r = cw * kRowsPerLoader + i;
-                const uint32_t hi = tf32_rna(cur[i]);
-                const uint32_t lo = tf32_rna(cur[i] - __uint_as_float(hi));
+                float x = cur[i];
+                // intensities: converted here, a chunk after their loads were issued
+                if (args.i0 > 0.0f && m0 + r < args.A && kc * kBK + lane < args.D)
+                    x = line_integral(x, args.i0, args.ln_i0);
+                const uint32_t hi = tf32_rna(x);
+                const uint32_t lo = tf32_rna(x - __uint_as_float(hi));
                 // 128-byte swizzle: 16-byte chunk (lane / 4) XOR (row mod 8)
                 const uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 +
                                                 ((((lane >> 2) ^ (r & 7)) << 4) | ((lane & 3) << 2)));
@@ -408,6 +415,8 @@ cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, cons
         a.pitch = p.pitch;
         a.nk = (p.D + kBK - 1) / kBK;
         a.m_tiles = (p.A + kBM - 1) / kBM;
+        a.i0 = p.i0f;
+        a.ln_i0 = p.ln_i0f;
         a.status = p.d_status;
         dim3 grid((p.pitch / 2 + kStep - 1) / kStep, a.m_tiles * cnt);
         filter_tc_kernel<<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);

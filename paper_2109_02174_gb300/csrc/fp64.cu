@@ -6,6 +6,7 @@
 // rate is a small fraction of its FP32 rate, so this path is for accuracy, not
 // throughput.
 #include "fbp_internal.h"
+#include "lambert.cuh"
 
 namespace fbp {
 namespace {
@@ -13,7 +14,7 @@ namespace {
 __global__ void __launch_bounds__(256)
     filter_direct_f64_kernel(const double *__restrict__ sino, int ld,
                              const double *__restrict__ taps, double *__restrict__ q, int D,
-                             int pitch)
+                             int pitch, double i0)
 {
     extern __shared__ double smd[];
     double *st = smd;                // taps tau*h(m), index m + D - 1
@@ -21,7 +22,8 @@ __global__ void __launch_bounds__(256)
     double *sq = sp + D;             // sq[k + 1] = Q[k], sq[0] = sq[D + 1] = 0
     const int i = blockIdx.x;
     for (int t = threadIdx.x; t < 2 * D - 1; t += blockDim.x) st[t] = taps[t];
-    for (int t = threadIdx.x; t < D; t += blockDim.x) sp[t] = sino[(size_t)i * ld + t];
+    for (int t = threadIdx.x; t < D; t += blockDim.x)
+        sp[t] = line_integral(sino[(size_t)i * ld + t], i0);
     if (threadIdx.x == 0) {
         sq[0] = 0.0;
         sq[D + 1] = 0.0;
@@ -80,7 +82,8 @@ cudaError_t launch_filter_direct_f64(const Plan &p, const double *sino, int ld, 
     cudaError_t e = cudaFuncSetAttribute(filter_direct_f64_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    filter_direct_f64_kernel<<<p.A, 256, smem, s>>>(sino, ld, p.d_taps64, q, p.D, p.pitch);
+    filter_direct_f64_kernel<<<p.A, 256, smem, s>>>(sino, ld, p.d_taps64, q, p.D, p.pitch,
+                                                     p.i0);
     return cudaGetLastError();
 }
 

@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_options_default_and_null_checks(lib):
     import paper_2109_02174_gb300 as fbp
     o = fbp.fbp_options_default()
-    assert (o.dtype, o.q_storage, o.accumulate, o.filter_path) == (0, 0, 0, 0)
+    assert (o.dtype, o.q_storage, o.accumulate, o.filter_path, o.i0) == (0, 0, 0, 0, 0.0)
     assert lib.fbp_options_default(None) == fbp.FBP_ERR_INVALID_ARG
     assert "NULL" in fbp.fbp_last_error()
     assert lib.fbp_plan(None, 8, 8, 8, None, 1.0, 0, None) == fbp.FBP_ERR_INVALID_ARG

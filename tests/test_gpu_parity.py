@@ -322,6 +322,52 @@ def test_fp64_rejects_fp32_only_options(fbp):
     assert e.value.status == fbp.FBP_ERR_UNSUPPORTED
 
 
+# ---------------------------------------------------------------- Eq. 1 on load
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("i0", [1e4, 5.0])
+def test_intensity_input_matches_oracle(fbp, path, i0):
+    """Photon counts in (plan option i0): each filter route converts them to
+    line integrals -ln(max(I, 1)/i0) as it loads them; the image matches the
+    oracle's conversion followed by its FBP.  At i0 = 5 many rays count zero
+    photons, which exercises the one-count floor."""
+    import torch
+    spec = synthetic.SliceSpec(200, 180, synthetic.det_for(200), 8, seed=31, filter=1, i0=i0,
+                               noise_seed=131)
+    th = synthetic.default_angles(spec.n_angles)
+    counts = synthetic.photon_counts(spec, th)
+    if i0 < 100:
+        assert (counts == 0).sum() > 200
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
+                    filter_path=PATHS[path], i0=i0)
+    img = plan.reconstruct(torch.from_numpy(counts.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    plan.device_status()
+    ref = oracle.fbp(oracle.lambert_beer(counts, i0), th, 1.0, spec.filter, spec.n_pix,
+                     nthreads=NTHREADS)
+    assert_parity(img.cpu().numpy(), ref)
+
+
+def test_intensity_input_fp64_path(fbp):
+    import torch
+    spec = synthetic.SliceSpec(96, 90, synthetic.det_for(96), 6, seed=32, filter=0, i0=50.0,
+                               noise_seed=132)
+    th = synthetic.default_angles(spec.n_angles)
+    counts = synthetic.photon_counts(spec, th)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=0, dtype=1, i0=50.0)
+    img = plan.reconstruct(torch.from_numpy(counts).cuda())
+    torch.cuda.synchronize()
+    ref = oracle.fbp(oracle.lambert_beer(counts, 50.0), th, 1.0, 0, spec.n_pix)
+    got = img.cpu().numpy()
+    assert np.abs(got - ref).max() <= FP64_REL * np.abs(ref).max()
+
+
+def test_intensity_option_rejects_bad_i0(fbp):
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(fbp.FbpError) as e:
+            fbp.Plan(32, 8, 46, i0=bad)
+        assert e.value.status == fbp.FBP_ERR_INVALID_ARG
+
+
 # ---------------------------------------------------------------- projector
 def test_radon_forward_matches_oracle(fbp):
     n, A = 57, 33
