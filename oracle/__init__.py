@@ -77,6 +77,10 @@ def _load():
             lib.oracle_fbp.restype = i
             lib.oracle_lambert_beer.argtypes = [d, ctypes.c_long, ctypes.c_double, d]
             lib.oracle_lambert_beer.restype = None
+            lib.oracle_psnr.argtypes = [d, d, i, i, d]
+            lib.oracle_psnr.restype = None
+            lib.oracle_ssim.argtypes = [d, d, i, i, ctypes.c_double]
+            lib.oracle_ssim.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -105,6 +109,26 @@ def lambert_beer(I, i0: float) -> np.ndarray:
     p = np.empty_like(I)
     _load().oracle_lambert_beer(_dp(I), int(I.size), float(i0), _dp(p))
     return p
+
+
+def psnr(x, y) -> tuple[float, float, float]:
+    """Eq. 3 of image x against reference y (2-D): (PSNR dB, MSE, MAX = max|y|)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert x.shape == y.shape and x.ndim == 2
+    out = np.empty(3)
+    _load().oracle_psnr(_dp(x), _dp(y), x.shape[0], x.shape[1], _dp(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def ssim(x, y, dynamic_range: float = 0.0) -> float:
+    """Eq. 4, mean over 11x11 Gaussian (sigma 1.5) windows, C1 = (0.01 L)^2,
+    C2 = (0.03 L)^2; L <= 0 takes max(y) - min(y)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert x.shape == y.shape and x.ndim == 2
+    return float(_load().oracle_ssim(_dp(x), _dp(y), x.shape[0], x.shape[1],
+                                     float(dynamic_range)))
 
 
 def taps(kind: int, n_det: int, tau: float = 1.0) -> np.ndarray:

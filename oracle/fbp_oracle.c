@@ -294,3 +294,86 @@ int oracle_fbp(const double *P, int n_angles, int n_det, int ld,
     free(Q);
     return 0;
 }
+
+/*
+ * PSNR (Eq. 3): 20 log10(MAX / sqrt(MSE)) of an image x against a reference
+ * y, both rows x cols (row-major, contiguous).  The paper leaves MAX open;
+ * here MAX = max |y|.  Identical images give +inf (MSE = 0), as the paper
+ * notes.  out[0] = PSNR in dB, out[1] = MSE, out[2] = MAX.
+ */
+void oracle_psnr(const double *x, const double *y, int rows, int cols, double *out)
+{
+    double se = 0.0, mx = 0.0;
+    const long n = (long)rows * cols;
+    for (long k = 0; k < n; ++k) {
+        const double d = x[k] - y[k];
+        se += d * d;
+        if (fabs(y[k]) > mx) mx = fabs(y[k]);
+    }
+    const double mse = se / (double)n;
+    out[0] = mse > 0.0 ? 20.0 * log10(mx / sqrt(mse)) : INFINITY;
+    out[1] = mse;
+    out[2] = mx;
+}
+
+/*
+ * SSIM (Eq. 4) with the constants and window the paper leaves open taken from
+ * Wang, Bovik, Sheikh & Simoncelli (2004): an 11 x 11 circular Gaussian window
+ * of standard deviation 1.5 (weights normalised to sum 1), C1 = (0.01 L)^2,
+ * C2 = (0.03 L)^2, and the image SSIM is the mean over every window that lies
+ * inside the image.  L is the dynamic range; L <= 0 takes max(y) - min(y) of
+ * the reference.  Per window:
+ *     mu_x = sum w x,  sigma_x^2 = sum w (x - mu_x)^2,
+ *     sigma_xy = sum w (x - mu_x)(y - mu_y),
+ *     SSIM = (2 mu_x mu_y + C1)(2 sigma_xy + C2)
+ *            / ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2)).
+ * Returns the mean SSIM (NaN if the image is smaller than the window).
+ */
+double oracle_ssim(const double *x, const double *y, int rows, int cols, double L)
+{
+    enum { W = 11, R = 5 };
+    if (rows < W || cols < W) return NAN;
+    if (L <= 0.0) {
+        double lo = y[0], hi = y[0];
+        for (long k = 1; k < (long)rows * cols; ++k) {
+            if (y[k] < lo) lo = y[k];
+            if (y[k] > hi) hi = y[k];
+        }
+        L = hi - lo;
+    }
+    const double c1 = (0.01 * L) * (0.01 * L), c2 = (0.03 * L) * (0.03 * L);
+    double w[W][W], wsum = 0.0;
+    for (int a = 0; a < W; ++a)
+        for (int b = 0; b < W; ++b) {
+            const double d2 = (double)((a - R) * (a - R) + (b - R) * (b - R));
+            w[a][b] = exp(-d2 / (2.0 * 1.5 * 1.5));
+            wsum += w[a][b];
+        }
+    for (int a = 0; a < W; ++a)
+        for (int b = 0; b < W; ++b) w[a][b] /= wsum;
+    double total = 0.0;
+    long count = 0;
+    for (int i = 0; i + W <= rows; ++i) {
+        for (int j = 0; j + W <= cols; ++j) {
+            double mx = 0.0, my = 0.0;
+            for (int a = 0; a < W; ++a)
+                for (int b = 0; b < W; ++b) {
+                    mx += w[a][b] * x[(long)(i + a) * cols + (j + b)];
+                    my += w[a][b] * y[(long)(i + a) * cols + (j + b)];
+                }
+            double vx = 0.0, vy = 0.0, cxy = 0.0;
+            for (int a = 0; a < W; ++a)
+                for (int b = 0; b < W; ++b) {
+                    const double dx = x[(long)(i + a) * cols + (j + b)] - mx;
+                    const double dy = y[(long)(i + a) * cols + (j + b)] - my;
+                    vx += w[a][b] * dx * dx;
+                    vy += w[a][b] * dy * dy;
+                    cxy += w[a][b] * dx * dy;
+                }
+            total += ((2.0 * mx * my + c1) * (2.0 * cxy + c2)) /
+                     ((mx * mx + my * my + c1) * (vx + vy + c2));
+            ++count;
+        }
+    }
+    return total / (double)count;
+}

@@ -31,6 +31,14 @@ MUTATIONS = [
     ("Lambert-Beer without the one-count floor", "const double v = I[k] > 1.0 ? I[k] : 1.0;",
      "const double v = I[k];"),
     ("Lambert-Beer sign", "p[k] = -log(v / i0);", "p[k] = log(v / i0);"),
+    ("PSNR with 10 log10", "out[0] = mse > 0.0 ? 20.0 * log10(", "out[0] = mse > 0.0 ? 10.0 * log10("),
+    ("PSNR peak taken from the image", "if (fabs(y[k]) > mx) mx = fabs(y[k]);",
+     "if (fabs(x[k]) > mx) mx = fabs(x[k]);"),
+    ("SSIM window sigma 1", "w[a][b] = exp(-d2 / (2.0 * 1.5 * 1.5));",
+     "w[a][b] = exp(-d2 / (2.0 * 1.0 * 1.0));"),
+    ("SSIM C2 from K1", "c2 = (0.03 * L) * (0.03 * L);", "c2 = (0.01 * L) * (0.01 * L);"),
+    ("SSIM covariance without its factor 2", "((2.0 * mx * my + c1) * (2.0 * cxy + c2))",
+     "((2.0 * mx * my + c1) * (cxy + c2))"),
 ]
 
 

@@ -280,3 +280,61 @@ def test_lambert_beer_round_trip_and_floor():
     assert np.allclose(oracle.lambert_beer(8.0 * counts, 8.0 * i0),
                        oracle.lambert_beer(counts, i0), rtol=0, atol=1e-12)
     assert oracle.lambert_beer(counts, i0).shape == counts.shape
+
+
+# ------------------------------------------------ quality metrics (Eqs. 3, 4)
+def test_psnr_closed_forms():
+    """Eq. 3: identical images give +inf; an image off by a constant c from the
+    reference y has MSE = c^2, so PSNR = 20 log10(max|y| / |c|); scaling both
+    images leaves PSNR unchanged."""
+    y = np.random.default_rng(7).normal(size=(30, 41))
+    assert oracle.psnr(y, y)[0] == math.inf
+    db, mse, mx = oracle.psnr(y + 0.125, y)
+    assert mse == pytest.approx(0.125 ** 2, rel=1e-12)
+    assert mx == np.abs(y).max()
+    assert db == pytest.approx(20 * math.log10(np.abs(y).max() / 0.125), rel=1e-12)
+    x = y + np.random.default_rng(8).normal(scale=0.01, size=y.shape)
+    assert oracle.psnr(3.0 * x, 3.0 * y)[0] == pytest.approx(oracle.psnr(x, y)[0], rel=1e-12)
+
+
+def test_ssim_identity_symmetry_and_constant_images():
+    """Eq. 4: SSIM(x, x) = 1; SSIM is symmetric for a fixed L; two constant
+    images a and b have zero variances, so every window gives
+    (2ab + C1)/(a^2 + b^2 + C1) with C1 = (0.01 L)^2."""
+    rng = np.random.default_rng(9)
+    x = rng.random((37, 29))
+    y = x + rng.normal(scale=0.05, size=x.shape)
+    assert oracle.ssim(x, x, 1.0) == pytest.approx(1.0, abs=1e-14)
+    assert oracle.ssim(x, y, 1.0) == pytest.approx(oracle.ssim(y, x, 1.0), abs=1e-14)
+    a, b, L = 0.7, 0.4, 2.0
+    c1 = (0.01 * L) ** 2
+    got = oracle.ssim(np.full((20, 16), a), np.full((20, 16), b), L)
+    assert got == pytest.approx((2 * a * b + c1) / (a * a + b * b + c1), rel=1e-12)
+
+
+def test_ssim_dynamic_range_defaults_to_reference_span():
+    rng = np.random.default_rng(10)
+    y = rng.random((24, 24)) * 3.0 - 1.0
+    x = y + rng.normal(scale=0.1, size=y.shape)
+    assert oracle.ssim(x, y) == pytest.approx(oracle.ssim(x, y, y.max() - y.min()), rel=1e-14)
+
+
+def test_ssim_window_from_an_impulse():
+    """The window (Wang et al. 2004: 11 x 11 Gaussian, sigma 1.5, normalised),
+    probed with an impulse: x is zero but for a 1 at the centre of a 31 x 31
+    image, y is zero.  Windows that miss the impulse compare two zero patches
+    (SSIM 1); a window holding it at offset (a, b) has mu_x = w_ab,
+    sigma_x^2 = w_ab (1 - w_ab), mu_y = sigma_y = sigma_xy = 0, so its SSIM is
+    C1 C2 / ((w_ab^2 + C1)(w_ab (1 - w_ab) + C2)); 121 of the 441 windows hold it."""
+    n, L = 31, 1.0
+    x = np.zeros((n, n))
+    x[15, 15] = 1.0
+    y = np.zeros((n, n))
+    c1, c2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+    d = np.arange(11) - 5
+    g = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2 * 1.5 ** 2))
+    w = g / g.sum()
+    s = c1 * c2 / ((w ** 2 + c1) * (w * (1 - w) + c2))
+    want = (441 - 121 + s.sum()) / 441
+    assert oracle.ssim(x, y, L) == pytest.approx(want, rel=1e-12)
+    assert math.isnan(oracle.ssim(np.zeros((10, 30)), np.zeros((10, 30)), 1.0))
