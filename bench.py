@@ -307,7 +307,9 @@ def run_configs(fbp):
     through fbp_reconstruct (the plain path), L2 flushed before each call:
     the plain slice (256^2, 180 angles, 363 bins, Ram-Lak, FFT length 1024),
     the float-vs-double slice on the FP64 path (against the nominal FP64 rate),
-    and the large slice (2048^2, 2048 angles, 2899 bins) with the filter time
+    PSNR/SSIM (on the GPU) of the FP32, Kahan and FP16-pair images of the
+    float-vs-double slice against its FP64 image; and the large slice
+    (2048^2, 2048 angles, 2899 bins) with the filter time
     of the FFT and tensor-core routes and the speed of its FP16-pair and Kahan
     variants; and the batched filter of 64 float-vs-double slices fed line
     integrals or photon counts (Lambert-Beer conversion on load)."""
@@ -339,8 +341,20 @@ def run_configs(fbp):
                                 "gupdates_per_s": spec.updates / (ms / 1e3) / 1e9,
                                 "path": "fbp_reconstruct, FP32, FFT length 1024"}
     spec = synthetic.cfg_float_double()
-    _, _, ms = one_slice(spec, dtype=1, reps=5)
+    p64, s64, ms = one_slice(spec, dtype=1, reps=5)
     gups = spec.updates / (ms / 1e3) / 1e9
+    # the paper's comparison measures (Eqs. 3, 4) on the device: each FP32
+    # variant's image against the FP64 path's image of the same slice
+    img64 = p64.reconstruct(s64).float()
+    s32 = s64.float()
+    quality = {}
+    for name, opt in (("fp32", {}), ("fp32_kahan", {"accumulate": 1}),
+                      ("fp16_pairs", {"q_storage": 2})):
+        img = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
+                       **opt).reconstruct(s32)
+        db, ss = fbp.quality(img, img64)
+        quality[name] = {"psnr_db": db, "ssim": ss}
+    out["quality_vs_fp64_512x720x725"] = quality
     fp64_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2 / OPS_PER_UPDATE / 1e9
     out["fp64_512x720x725"] = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
                                "gupdates_per_s": gups, "fp64_peak_gupdates_per_s": fp64_peak,

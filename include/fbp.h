@@ -321,6 +321,33 @@ fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
                         fbp_filter_type filter, const fbp_options *base, int batch,
                         fbp_tuning *out);
 
+/* ------------------------------------------------------------------ quality
+ * PSNR (Eq. 3) and SSIM (Eq. 4) of an image against a reference on the device:
+ * the measures the paper compares its reconstructions with (section
+ * "Benchmark").  The paper leaves PSNR's MAX and SSIM's window and constants
+ * open; here
+ *   PSNR = 20 log10(MAX / sqrt(MSE)), MAX = max |reference|, +inf when the
+ *          images are identical;
+ *   SSIM = mean over every 11 x 11 window inside the image of
+ *          (2 mu_x mu_y + C1)(2 sigma_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2))
+ *          with Gaussian window weights (sigma 1.5, normalised), C1 = (0.01 L)^2,
+ *          C2 = (0.03 L)^2 (Wang, Bovik, Sheikh & Simoncelli 2004); L is
+ *          dynamic_range, or the reference's max - min when dynamic_range <= 0;
+ *          NaN when rows or cols < 11.
+ * Every sum is taken in a fixed order: the results are the same bits every run. */
+
+/* Device scratch fbp_quality needs for a rows x cols image, in *bytes. */
+fbp_status fbp_quality_scratch_bytes(int rows, int cols, size_t *bytes);
+
+/* image, reference: device [rows][ld] float (ld >= cols, 16-byte aligned);
+ * scratch: device, >= fbp_quality_scratch_bytes; out: device, 2 doubles,
+ * out[0] = PSNR in dB, out[1] = SSIM.  Asynchronous on `stream`; allocates
+ * nothing.  FBP_ERR_INVALID_ARG for bad sizes, NULL buffers, a short scratch
+ * or a non-finite dynamic_range; FBP_ERR_ALIGNMENT for unaligned buffers. */
+fbp_status fbp_quality(const void *image, const void *reference, int rows, int cols, int ld,
+                       double dynamic_range, void *scratch, size_t scratch_bytes, double *out,
+                       fbp_stream_t stream);
+
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

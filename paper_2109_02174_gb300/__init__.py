@@ -94,6 +94,8 @@ _SIGS = {
                               ctypes.POINTER(fbp_batch_io), _I, _P],
     "fbp_batch_launch": [_P, _P],
     "fbp_batch_kernel_count": [_P, ctypes.POINTER(_I)],
+    "fbp_quality_scratch_bytes": [_I, _I, ctypes.POINTER(ctypes.c_size_t)],
+    "fbp_quality": [_P, _P, _I, _I, _I, ctypes.c_double, _P, ctypes.c_size_t, _P, _P],
     "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
     "fbp_autotune": [_I, _I, _I, ctypes.c_double, _I, ctypes.POINTER(fbp_options), _I,
                      ctypes.POINTER(fbp_tuning)],
@@ -265,6 +267,38 @@ def fbp_autotune(n_pix, n_angles, n_det, det_spacing=1.0, filter=FBP_FILTER_RAM_
     d = {name: getattr(t.options, name) for name, _ in fbp_options._fields_}
     d.update(filter_ms=t.filter_ms, backproject_ms=t.backproject_ms, from_cache=t.from_cache)
     return d
+
+
+def fbp_quality_scratch_bytes(rows: int, cols: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().fbp_quality_scratch_bytes(int(rows), int(cols), ctypes.byref(n)))
+    return n.value
+
+
+def quality(image, reference, dynamic_range: float = 0.0, stream=None) -> tuple[float, float]:
+    """(PSNR dB, SSIM) of a 2-D float32 device image against a reference of
+    the same shape and row stride, computed on the GPU (see fbp.h: Eq. 3 with
+    MAX = max|reference|; Eq. 4 with 11x11 Gaussian windows, sigma 1.5,
+    K1 = 0.01, K2 = 0.03; L = dynamic_range or the reference's span).
+    Synchronises the stream to return the values."""
+    import torch
+    assert image.shape == reference.shape and image.dim() == 2
+    assert image.stride(1) == 1 and reference.stride(1) == 1
+    assert image.stride(0) == reference.stride(0)
+    rows, cols = image.shape
+    scratch = torch.empty(fbp_quality_scratch_bytes(rows, cols), dtype=torch.uint8,
+                          device=image.device)
+    out = torch.empty(2, dtype=torch.float64, device=image.device)
+    s = _stream(stream)
+    _check(load_library().fbp_quality(_ptr(image), _ptr(reference), rows, cols, image.stride(0),
+                                      float(dynamic_range), _ptr(scratch), scratch.numel(),
+                                      _ptr(out), s))
+    if stream is None:
+        torch.cuda.current_stream().synchronize()
+    else:
+        stream.synchronize()
+    v = out.cpu()
+    return float(v[0]), float(v[1])
 
 
 # ------------------------------------------------------------ tensor wrapper

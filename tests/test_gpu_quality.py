@@ -1,0 +1,99 @@
+"""GPU: PSNR (Eq. 3) and SSIM (Eq. 4) on the device match the FP64 oracle's
+on the same float32 images: reconstructions against the oracle's image, a
+precision variant against the FP32 path, identical images, ragged shapes with
+a row stride, images smaller than the SSIM window; the same bits every run."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+SSIM_ATOL = 2e-5   # FP32 local statistics (the oracle works in FP64)
+PSNR_RTOL = 1e-9   # squared differences formed exactly, summed in FP64
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_02174_gb300 import build
+    build.build()
+    import paper_2109_02174_gb300 as m
+    return m
+
+
+def _check(fbp, x, y, rng=0.0):
+    import torch
+    got = fbp.quality(x, y, rng)
+    xs = x.double().cpu().numpy()
+    ys = y.double().cpu().numpy()
+    want_psnr = oracle.psnr(xs, ys)[0]
+    want_ssim = oracle.ssim(xs, ys, rng)
+    if math.isinf(want_psnr):
+        assert math.isinf(got[0])
+    else:
+        assert got[0] == pytest.approx(want_psnr, rel=PSNR_RTOL)
+    if math.isnan(want_ssim):
+        assert math.isnan(got[1])
+    else:
+        assert abs(got[1] - want_ssim) <= SSIM_ATOL, (got[1], want_ssim)
+    return got
+
+
+def test_reconstruction_against_oracle_image(fbp):
+    import torch
+    spec = synthetic.cfg_plain()
+    th = synthetic.default_angles(spec.n_angles)
+    sino = synthetic.sinogram(spec, th)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter)
+    img = plan.reconstruct(torch.from_numpy(sino.astype(np.float32)).cuda())
+    ref = oracle.fbp(sino.astype(np.float32).astype(np.float64), th, 1.0, spec.filter, spec.n_pix)
+    ref_t = torch.from_numpy(ref.astype(np.float32)).cuda()
+    db, s = _check(fbp, img, ref_t)
+    assert db > 80 and s > 0.9999  # FP32 path against the FP64 oracle
+
+
+def test_fp16_pairs_against_fp32(fbp):
+    import torch
+    spec = synthetic.cfg_float_double()
+    sino = torch.from_numpy(synthetic.sinogram(spec).astype(np.float32)).cuda()
+    a = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter).reconstruct(sino)
+    b = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
+                 q_storage=2).reconstruct(sino)
+    _check(fbp, b, a)
+    _check(fbp, b, a, rng=2.0)
+
+
+def test_identical_ragged_small_and_deterministic(fbp):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(3)
+    wide = torch.rand((37, 64), device="cuda", generator=g)
+    x = wide[:, :53]                     # row stride 64 > 53 columns
+    wide2 = wide + 0.05 * torch.rand((37, 64), device="cuda", generator=g)
+    y = wide2[:, :53]
+    db, s = _check(fbp, x, x)
+    assert math.isinf(db) and s == pytest.approx(1.0, abs=1e-6)
+    first = _check(fbp, x, y)
+    assert fbp.quality(x, y) == first  # same bits
+    small = torch.rand((10, 40), device="cuda", generator=g)
+    _check(fbp, small, small * 0.9)      # no window fits: SSIM NaN
+
+
+def test_quality_argument_errors(fbp):
+    import torch
+    x = torch.zeros((16, 16), device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    lib = fbp.load_library()
+    need = fbp.fbp_quality_scratch_bytes(16, 16)
+    sc = torch.zeros(need, dtype=torch.uint8, device="cuda")
+    s = int(torch.cuda.current_stream().cuda_stream)
+    assert lib.fbp_quality(x.data_ptr(), x.data_ptr(), 16, 16, 16, 0.0, sc.data_ptr(), need - 1,
+                           out.data_ptr(), s) == fbp.FBP_ERR_INVALID_ARG
+    assert lib.fbp_quality(x.data_ptr(), x.data_ptr(), 16, 16, 8, 0.0, sc.data_ptr(), need,
+                           out.data_ptr(), s) == fbp.FBP_ERR_INVALID_ARG
+    assert lib.fbp_quality(x.data_ptr() + 4, x.data_ptr(), 16, 15, 16, 0.0, sc.data_ptr(), need,
+                           out.data_ptr(), s) == fbp.FBP_ERR_ALIGNMENT
