@@ -81,6 +81,8 @@ def _load():
             lib.oracle_psnr.restype = None
             lib.oracle_ssim.argtypes = [d, d, i, i, ctypes.c_double]
             lib.oracle_ssim.restype = ctypes.c_double
+            lib.oracle_volume.argtypes = [d, i, d, i, d, i, d]
+            lib.oracle_volume.restype = i
             _lib = lib
     return _lib
 
@@ -129,6 +131,20 @@ def ssim(x, y, dynamic_range: float = 0.0) -> float:
     assert x.shape == y.shape and x.ndim == 2
     return float(_load().oracle_ssim(_dp(x), _dp(y), x.shape[0], x.shape[1],
                                      float(dynamic_range)))
+
+
+def volume(slices, z, z_out) -> np.ndarray:
+    """Linear interpolation along z of a slice stack [K][n][n] at positions z
+    (strictly increasing) onto planes z_out (inside [z[0], z[-1]]): [M][n][n]."""
+    S = _f64(slices)
+    z = _f64(z)
+    zo = _f64(z_out)
+    K, n, n2 = S.shape
+    assert n == n2 and z.shape == (K,)
+    out = np.empty((zo.size, n, n))
+    if _load().oracle_volume(_dp(S), K, _dp(z), n, _dp(zo), zo.size, _dp(out)) != 0:
+        raise ValueError("volume: z not increasing or a plane outside the stack")
+    return out
 
 
 def taps(kind: int, n_det: int, tau: float = 1.0) -> np.ndarray:

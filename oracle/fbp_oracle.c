@@ -377,3 +377,34 @@ double oracle_ssim(const double *x, const double *y, int rows, int cols, double 
     }
     return total / (double)count;
 }
+
+/*
+ * A 3D volume from a stack of reconstructed 2D slices by interpolation along
+ * z (section "Introduction": 3D images from the interpolation of a stack of
+ * 2D images; the paper gives no rule, linear interpolation is read here).
+ * K slices of n x n pixels at strictly increasing positions z[k]; M output
+ * planes at zo[m], each inside [z[0], z[K-1]]: plane m = (1 - t) S_k + t S_{k+1}
+ * with z[k] <= zo[m] <= z[k+1] and t = (zo[m] - z[k]) / (z[k+1] - z[k]).
+ * Returns 0, or -1 for a plane outside the stack or non-increasing z.
+ */
+int oracle_volume(const double *slices, int K, const double *z, int n, const double *zo, int M,
+                  double *out)
+{
+    for (int k = 1; k < K; ++k)
+        if (!(z[k] > z[k - 1])) return -1;
+    const long np = (long)n * n;
+    for (int m = 0; m < M; ++m) {
+        if (zo[m] < z[0] || zo[m] > z[K - 1]) return -1;
+        int k = 0;
+        while (k + 1 < K - 1 && zo[m] > z[k + 1]) ++k;
+        if (K == 1) {
+            for (long p = 0; p < np; ++p) out[(long)m * np + p] = slices[p];
+            continue;
+        }
+        const double t = (zo[m] - z[k]) / (z[k + 1] - z[k]);
+        for (long p = 0; p < np; ++p)
+            out[(long)m * np + p] = (1.0 - t) * slices[(long)k * np + p] +
+                                    t * slices[(long)(k + 1) * np + p];
+    }
+    return 0;
+}

@@ -39,6 +39,10 @@ MUTATIONS = [
     ("SSIM C2 from K1", "c2 = (0.03 * L) * (0.03 * L);", "c2 = (0.01 * L) * (0.01 * L);"),
     ("SSIM covariance without its factor 2", "((2.0 * mx * my + c1) * (2.0 * cxy + c2))",
      "((2.0 * mx * my + c1) * (cxy + c2))"),
+    ("volume weights swapped", "out[(long)m * np + p] = (1.0 - t) * slices[(long)k * np + p] +",
+     "out[(long)m * np + p] = t * slices[(long)k * np + p] +"),
+    ("volume picks the wrong interval", "while (k + 1 < K - 1 && zo[m] > z[k + 1]) ++k;",
+     "while (k + 1 < K - 1 && zo[m] >= z[k]) ++k;"),
 ]
 
 

@@ -338,3 +338,30 @@ def test_ssim_window_from_an_impulse():
     want = (441 - 121 + s.sum()) / 441
     assert oracle.ssim(x, y, L) == pytest.approx(want, rel=1e-12)
     assert math.isnan(oracle.ssim(np.zeros((10, 30)), np.zeros((10, 30)), 1.0))
+
+
+# ------------------------------------------------ volume from a slice stack
+def test_volume_is_exact_on_fields_linear_in_z():
+    """Linear interpolation reproduces any field linear in z, on uneven slice
+    spacing too: slices A + z_k B give planes A + z B at every z."""
+    rng = np.random.default_rng(11)
+    n = 6
+    A, B = rng.normal(size=(n, n)), rng.normal(size=(n, n))
+    z = np.array([0.0, 0.7, 1.1, 2.5, 4.0])
+    zo = np.array([0.0, 0.35, 1.1, 1.9, 3.99, 4.0])
+    vol = oracle.volume(A + z[:, None, None] * B, z, zo)
+    assert np.allclose(vol, A + zo[:, None, None] * B, rtol=0, atol=1e-13)
+
+
+def test_volume_hits_slices_and_midpoints_and_rejects_outside():
+    rng = np.random.default_rng(12)
+    S = rng.normal(size=(4, 5, 5))
+    z = np.array([1.0, 2.0, 3.0, 5.0])
+    vol = oracle.volume(S, z, np.array([2.0, 5.0, 1.5, 4.0]))
+    assert np.array_equal(vol[0], S[1]) and np.array_equal(vol[1], S[3])
+    assert np.allclose(vol[2], 0.5 * (S[0] + S[1]), atol=1e-15)
+    assert np.allclose(vol[3], 0.5 * (S[2] + S[3]), atol=1e-15)
+    with pytest.raises(ValueError):
+        oracle.volume(S, z, np.array([0.5]))
+    with pytest.raises(ValueError):
+        oracle.volume(S, np.array([1.0, 2.0, 2.0, 3.0]), np.array([1.5]))
