@@ -311,8 +311,9 @@ def run_configs(fbp):
     float-vs-double slice against its FP64 image; and the large slice
     (2048^2, 2048 angles, 2899 bins) with the filter time
     of the FFT and tensor-core routes and the speed of its FP16-pair and Kahan
-    variants; and the batched filter of 64 float-vs-double slices fed line
-    integrals or photon counts (Lambert-Beer conversion on load)."""
+    variants; the batched filter of 64 float-vs-double slices fed line
+    integrals or photon counts (Lambert-Beer conversion on load); and a volume
+    interpolated from a stack of 64 slices."""
     import torch
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
@@ -388,6 +389,32 @@ def run_configs(fbp):
         lb[name] = _timed_flushed(fbatch.launch, 5, stream, flush) / 64 * 1e3
         fbatch.close()
     out["lambert_beer_on_load_us_per_slice"] = lb
+    # a volume from a stack of 64 reconstructed 512^2 slices, four planes per
+    # gap (253 planes): an HBM-bound stream; minimal bytes = slices read once
+    # + planes written once
+    import ctypes
+    K, n = 64, 512
+    zs = np.arange(K, dtype=np.float64)
+    zo = np.linspace(0.0, K - 1.0, 4 * (K - 1) + 1)
+    slices = [torch.randn((n, n), device="cuda") for _ in range(K)]
+    vol = torch.empty((zo.size, n, n), device="cuda")
+    c_ptrs = (ctypes.c_void_p * K)(*[t.data_ptr() for t in slices])
+    c_z = (ctypes.c_double * K)(*zs)
+    c_zo = (ctypes.c_double * zo.size)(*zo)
+    lib = fbp.load_library()
+
+    def vol_call():
+        lib.fbp_volume_from_slices(c_ptrs, K, c_z, n, c_zo, zo.size, vol.data_ptr(), sp)
+    vol_call()
+    torch.cuda.synchronize()
+    vms = _timed_flushed(vol_call, 5, stream, flush)
+    vbytes = (K + zo.size) * n * n * 4
+    pk, _ = peaks()
+    out["volume_64x512_to_253_planes"] = {
+        "ms": vms, "gb_per_s_min_bytes": vbytes / (vms / 1e3) / 1e9,
+        "hbm_peak_gbs": pk["hbm_gbs"],
+        "frac_of_hbm": vbytes / (vms / 1e3) / 1e9 / pk["hbm_gbs"],
+        "min_bytes": vbytes}
     entry["variants_gupdates_per_s"] = {}
     for name, opt in (("fp16_pairs", {"q_storage": 2}), ("kahan", {"accumulate": 1})):
         _, _, vms = one_slice(spec, reps=5, **opt)

@@ -348,6 +348,23 @@ fbp_status fbp_quality(const void *image, const void *reference, int rows, int c
                        double dynamic_range, void *scratch, size_t scratch_bytes, double *out,
                        fbp_stream_t stream);
 
+/* ------------------------------------------------------------------ volume
+ * A 3D volume from a stack of reconstructed 2D slices by interpolation along z
+ * (section "Introduction": 3D CT images from the interpolation of a stack of
+ * 2D images; the paper gives no rule, linear interpolation is used):
+ *     plane m = (1 - t) S_k + t S_{k+1},  z[k] <= z_out[m] <= z[k+1],
+ *     t = (z_out[m] - z[k]) / (z[k+1] - z[k]).
+ * slices: host array of n_slices device pointers, each an [n_pix][n_pix]
+ * float image (e.g. the images of a batch), 16-byte aligned; z: host,
+ * n_slices strictly increasing positions; z_out: host, n_planes positions in
+ * [z[0], z[n_slices-1]]; volume: device [n_planes][n_pix][n_pix] float,
+ * 16-byte aligned.  Asynchronous on `stream`; allocates nothing.
+ * FBP_ERR_INVALID_ARG for NULL/empty inputs, non-increasing z or a plane
+ * outside the stack; FBP_ERR_ALIGNMENT for unaligned buffers. */
+fbp_status fbp_volume_from_slices(const void *const *slices, int n_slices, const double *z,
+                                  int n_pix, const double *z_out, int n_planes, void *volume,
+                                  fbp_stream_t stream);
+
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

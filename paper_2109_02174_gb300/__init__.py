@@ -96,6 +96,8 @@ _SIGS = {
     "fbp_batch_kernel_count": [_P, ctypes.POINTER(_I)],
     "fbp_quality_scratch_bytes": [_I, _I, ctypes.POINTER(ctypes.c_size_t)],
     "fbp_quality": [_P, _P, _I, _I, _I, ctypes.c_double, _P, ctypes.c_size_t, _P, _P],
+    "fbp_volume_from_slices": [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_double), _I,
+                               ctypes.POINTER(ctypes.c_double), _I, _P, _P],
     "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
     "fbp_autotune": [_I, _I, _I, ctypes.c_double, _I, ctypes.POINTER(fbp_options), _I,
                      ctypes.POINTER(fbp_tuning)],
@@ -299,6 +301,25 @@ def quality(image, reference, dynamic_range: float = 0.0, stream=None) -> tuple[
         stream.synchronize()
     v = out.cpu()
     return float(v[0]), float(v[1])
+
+
+def volume(slices, z, z_out, out=None, stream=None):
+    """3D volume [M][n][n] (float32, device) from 2-D slices (device tensors
+    [n][n], e.g. Batch.images) at strictly increasing positions z, by linear
+    interpolation along z onto the planes z_out (inside [z[0], z[-1]])."""
+    import torch
+    slices = list(slices)
+    n = slices[0].shape[0]
+    for t in slices:
+        assert t.shape == (n, n) and t.dtype == torch.float32 and t.is_contiguous()
+    zs = (ctypes.c_double * len(slices))(*[float(v) for v in z])
+    zo = (ctypes.c_double * len(z_out))(*[float(v) for v in z_out])
+    ptrs = (_P * len(slices))(*[_ptr(t) for t in slices])
+    if out is None:
+        out = torch.empty((len(z_out), n, n), dtype=torch.float32, device=slices[0].device)
+    _check(load_library().fbp_volume_from_slices(ptrs, len(slices), zs, n, zo, len(z_out),
+                                                 _ptr(out), _stream(stream)))
+    return out
 
 
 # ------------------------------------------------------------ tensor wrapper
