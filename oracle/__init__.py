@@ -83,6 +83,9 @@ def _load():
             lib.oracle_ssim.restype = ctypes.c_double
             lib.oracle_volume.argtypes = [d, i, d, i, d, i, d]
             lib.oracle_volume.restype = i
+            lib.oracle_fdk.argtypes = [d, i, i, i, d, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, i, i, i, i, d, i]
+            lib.oracle_fdk.restype = i
             _lib = lib
     return _lib
 
@@ -145,6 +148,21 @@ def volume(slices, z, z_out) -> np.ndarray:
     if _load().oracle_volume(_dp(S), K, _dp(z), n, _dp(zo), zo.size, _dp(out)) != 0:
         raise ValueError("volume: z not increasing or a plane outside the stack")
     return out
+
+
+def fdk(P, beta, R: float, du: float, dv: float, kind: int, nx: int, ny: int, nz: int,
+        nthreads: int = 1) -> np.ndarray:
+    """FDK cone-beam reconstruction of projections P [A][nv][nu] (virtual
+    detector through the axis, source radius R) into f [nz][ny][nx]."""
+    P = _f64(P)
+    beta = _f64(beta)
+    A, nv, nu = P.shape
+    assert beta.shape == (A,)
+    f = np.empty((nz, ny, nx))
+    if _load().oracle_fdk(_dp(P), A, nv, nu, _dp(beta), float(R), float(du), float(dv),
+                          int(kind), nx, ny, nz, _dp(f), int(nthreads)) != 0:
+        raise ValueError("fdk: bad argument")
+    return f
 
 
 def taps(kind: int, n_det: int, tau: float = 1.0) -> np.ndarray:

@@ -408,3 +408,143 @@ int oracle_volume(const double *slices, int K, const double *z, int n, const dou
     }
     return 0;
 }
+
+/*
+ * FDK cone-beam reconstruction (Feldkamp, Davis & Kress 1984), the 3D
+ * extension the paper names as its future work (section "Conclusion").  The
+ * paper fixes no cone-beam geometry; the one read here:
+ *   - the source circles the z axis at radius R, at (R cos b, R sin b, 0) for
+ *     projection angle b, over a full turn (b_a given, 2 pi / A apart);
+ *   - projections live on a virtual flat detector through the rotation axis,
+ *     perpendicular to the central ray, with axes u along (-sin b, cos b, 0)
+ *     and v along z: P[a][i][j] at u_j = (j - (nu-1)/2) du, v_i = (i - (nv-1)/2) dv;
+ *   - voxel (ix, iy, iz) of an nx x ny x nz volume (f[iz][iy][ix]) has centre
+ *     (ix - (nx-1)/2, iy - (ny-1)/2, iz - (nz-1)/2), voxel size 1.
+ * Steps, in the order of the algorithm:
+ *   1. weight: P~ = P R / sqrt(R^2 + u^2 + v^2);
+ *   2. filter every detector row along u with the ramp taps (oracle_taps with
+ *      spacing du): Q[a][i][k] = du sum_j h(k - j) P~[a][i][j];
+ *   3. backproject: for every voxel and angle, s = x cos b + y sin b,
+ *      t = -x sin b + y cos b, U = R - s, the voxel projects to
+ *      u = R t / U, v = R z / U; Q is read there by bilinear interpolation
+ *      (zero outside the detector) and weighted by (R / U)^2; the sum over the
+ *      angles (in order) is scaled by (1/2)(2 pi / A) = pi / A, the 1/2 for the
+ *      two passes of a full turn over every line.
+ * As R grows the rays turn parallel, every weight tends to 1, u -> t and
+ * v -> z: the result tends to the parallel-beam FBP (Eq. 2) of each detector
+ * row at angles b + pi/2.  Returns 0, or -1 on a bad argument.
+ */
+typedef struct {
+    const double *Q;
+    const double *beta;
+    int A, nv, nu, nx, ny, nz, z0, z1;
+    double R, du, dv;
+    double *f;
+} fdk_job;
+
+static double fdk_sample(const double *row0, const double *row1, double w1, int nu, double ku)
+{
+    /* row0/row1: the two detector rows around v (NULL when outside);
+     * ku: column coordinate; linear in u then in v. */
+    const double fk = floor(ku);
+    const int k = (int)fk;
+    const double w = ku - fk;
+    double a = 0.0, b = 0.0;
+    if (row0) {
+        const double q0 = (k >= 0 && k < nu) ? row0[k] : 0.0;
+        const double q1 = (k + 1 >= 0 && k + 1 < nu) ? row0[k + 1] : 0.0;
+        a = (1.0 - w) * q0 + w * q1;
+    }
+    if (row1) {
+        const double q0 = (k >= 0 && k < nu) ? row1[k] : 0.0;
+        const double q1 = (k + 1 >= 0 && k + 1 < nu) ? row1[k + 1] : 0.0;
+        b = (1.0 - w) * q0 + w * q1;
+    }
+    return (1.0 - w1) * a + w1 * b;
+}
+
+static void *fdk_slices(void *arg)
+{
+    fdk_job *J = (fdk_job *)arg;
+    const long row_len = J->nu;
+    for (int iz = J->z0; iz < J->z1; ++iz) {
+        const double z = (double)iz - 0.5 * (double)(J->nz - 1);
+        for (int iy = 0; iy < J->ny; ++iy) {
+            const double y = (double)iy - 0.5 * (double)(J->ny - 1);
+            for (int ix = 0; ix < J->nx; ++ix) {
+                const double x = (double)ix - 0.5 * (double)(J->nx - 1);
+                double sum = 0.0;
+                for (int a = 0; a < J->A; ++a) {
+                    const double cb = cos(J->beta[a]), sb = sin(J->beta[a]);
+                    const double s = x * cb + y * sb, t = -x * sb + y * cb;
+                    const double U = J->R - s;
+                    const double u = J->R * t / U, v = J->R * z / U;
+                    const double ku = u / J->du + 0.5 * (double)(J->nu - 1);
+                    const double kv = v / J->dv + 0.5 * (double)(J->nv - 1);
+                    const double fv = floor(kv);
+                    const int i = (int)fv;
+                    const double wv = kv - fv;
+                    const double *base = J->Q + (long)a * J->nv * row_len;
+                    const double *r0 = (i >= 0 && i < J->nv) ? base + (long)i * row_len : NULL;
+                    const double *r1 = (i + 1 >= 0 && i + 1 < J->nv) ? base + (long)(i + 1) * row_len : NULL;
+                    const double q = fdk_sample(r0, r1, wv, J->nu, ku);
+                    sum += (J->R / U) * (J->R / U) * q;
+                }
+                J->f[((long)iz * J->ny + iy) * J->nx + ix] = sum * (M_PI / (double)J->A);
+            }
+        }
+    }
+    return NULL;
+}
+
+int oracle_fdk(const double *P, int A, int nv, int nu, const double *beta, double R, double du,
+               double dv, int kind, int nx, int ny, int nz, double *f, int nthreads)
+{
+    if (A < 1 || nv < 1 || nu < 1 || nx < 1 || ny < 1 || nz < 1 || !(R > 0.0) || !(du > 0.0) ||
+        !(dv > 0.0))
+        return -1;
+    const long rows = (long)A * nv;
+    double *h = (double *)malloc(sizeof(double) * (size_t)(2 * nu - 1));
+    double *Pw = (double *)malloc(sizeof(double) * (size_t)rows * (size_t)nu);
+    double *Q = (double *)malloc(sizeof(double) * (size_t)rows * (size_t)nu);
+    if (h == NULL || Pw == NULL || Q == NULL || oracle_taps(kind, nu, du, h) != 0) {
+        free(h);
+        free(Pw);
+        free(Q);
+        return -1;
+    }
+    /* 1. cosine weight */
+    for (int a = 0; a < A; ++a)
+        for (int i = 0; i < nv; ++i) {
+            const double v = ((double)i - 0.5 * (double)(nv - 1)) * dv;
+            for (int j = 0; j < nu; ++j) {
+                const double u = ((double)j - 0.5 * (double)(nu - 1)) * du;
+                const long k = ((long)a * nv + i) * nu + j;
+                Pw[k] = P[k] * R / sqrt(R * R + u * u + v * v);
+            }
+        }
+    /* 2. ramp filter along u, row by row */
+    oracle_filter_mt(Pw, (int)rows, nu, nu, h, du, Q, nthreads);
+    /* 3. weighted backprojection, slabs of z over threads */
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nz) nthreads = nz;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    fdk_job *jobs = (fdk_job *)malloc(sizeof(fdk_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        fdk_job J = {Q, beta, A, nv, nu, nx, ny, nz, (int)((long)nz * t / nthreads),
+                     (int)((long)nz * (t + 1) / nthreads), R, du, dv, f};
+        jobs[t] = J;
+        if (nthreads == 1)
+            fdk_slices(&jobs[t]);
+        else
+            pthread_create(&th[t], NULL, fdk_slices, &jobs[t]);
+    }
+    if (nthreads > 1)
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    free(jobs);
+    free(h);
+    free(Pw);
+    free(Q);
+    return 0;
+}

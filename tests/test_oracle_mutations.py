@@ -43,6 +43,16 @@ MUTATIONS = [
      "out[(long)m * np + p] = t * slices[(long)k * np + p] +"),
     ("volume picks the wrong interval", "while (k + 1 < K - 1 && zo[m] > z[k + 1]) ++k;",
      "while (k + 1 < K - 1 && zo[m] >= z[k]) ++k;"),
+    ("FDK distance weight (R/U) instead of (R/U)^2", "sum += (J->R / U) * (J->R / U) * q;",
+     "sum += (J->R / U) * q;"),
+    ("FDK cosine weight dropped", "Pw[k] = P[k] * R / sqrt(R * R + u * u + v * v);",
+     "Pw[k] = P[k];"),
+    ("FDK without the v magnification", "const double u = J->R * t / U, v = J->R * z / U;",
+     "const double u = J->R * t / U, v = z;"),
+    ("FDK without the u magnification", "const double u = J->R * t / U, v = J->R * z / U;",
+     "const double u = t, v = J->R * z / U;"),
+    ("FDK detector axis mirrored", "t = -x * sb + y * cb;", "t = x * sb - y * cb;"),
+    ("FDK scale for a half turn", "sum * (M_PI / (double)J->A)", "sum * (2.0 * M_PI / (double)J->A)"),
 ]
 
 
