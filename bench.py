@@ -389,6 +389,19 @@ def run_configs(fbp):
         lb[name] = _timed_flushed(fbatch.launch, 5, stream, flush) / 64 * 1e3
         fbatch.close()
     out["lambert_beer_on_load_us_per_slice"] = lb
+    # FDK cone-beam (the paper's future work): 256^3 voxels, 360 angles over a
+    # full turn, 448 x 320 detector, source radius 1024 voxels
+    fdk_plan = fbp.FdkPlan(360, 320, 448, 1024.0, 256, 256, 256)
+    proj = torch.randn((360, 320, 448), device="cuda")
+    fvol = torch.empty((256, 256, 256), device="cuda")
+    fws = torch.empty(fdk_plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    fdk_plan.reconstruct(proj, fvol, fws)
+    torch.cuda.synchronize()
+    fms = _timed_flushed(lambda: fdk_plan.reconstruct(proj, fvol, fws), 3, stream, flush)
+    fupd = 256 ** 3 * 360
+    out["fdk_256cubed_360x320x448"] = {"ms": fms, "voxel_updates_per_s": fupd / (fms / 1e3),
+                                       "gupdates_per_s": fupd / (fms / 1e3) / 1e9}
+    fdk_plan.close()
     # a volume from a stack of 64 reconstructed 512^2 slices, four planes per
     # gap (253 planes): an HBM-bound stream; minimal bytes = slices read once
     # + planes written once

@@ -99,7 +99,7 @@ fbp_status fbp_options_default(fbp_options *opt);
 /*
  * Create a plan on the current CUDA device.
  *   n_pix        image side, 1 .. 16384
- *   n_angles     projections, 1 .. 65535
+ *   n_angles     projections, 1 .. 16777216 (2^24)
  *   n_det        detector bins per projection, 1 .. 65535
  *   angles       host array of n_angles radians (copied), or NULL for
  *                th_i = i*pi/n_angles
@@ -364,6 +364,47 @@ fbp_status fbp_quality(const void *image, const void *reference, int rows, int c
 fbp_status fbp_volume_from_slices(const void *const *slices, int n_slices, const double *z,
                                   int n_pix, const double *z_out, int n_planes, void *volume,
                                   fbp_stream_t stream);
+
+/* ------------------------------------------------------------------ FDK
+ * Cone-beam 3D reconstruction by the algorithm of Feldkamp, Davis & Kress
+ * (1984), the extension the paper names as its future work (section
+ * "Conclusion").  The paper fixes no cone-beam geometry; this library's:
+ *   - the source circles the z axis at radius R, at (R cos b, R sin b, 0) for
+ *     projection angle b; a full turn (default b_a = 2 pi a / n_angles);
+ *   - projections lie on a virtual flat detector through the axis, u along
+ *     (-sin b, cos b, 0) and v along z: P[a][i][j] (float, device) at
+ *     u_j = (j - (nu-1)/2) du, v_i = (i - (nv-1)/2) dv;
+ *   - the volume f[nz][ny][nx] (float, device) has voxel size 1 and voxel
+ *     (ix, iy, iz) at (ix - (nx-1)/2, iy - (ny-1)/2, iz - (nz-1)/2); every
+ *     voxel must lie more than one unit inside the source circle.
+ * Steps: cosine weight R / sqrt(R^2 + u^2 + v^2), ramp filter along u (the
+ * filter of Q = P * H with spacing du), then for every voxel the sum over the
+ * angles of (R/U)^2 Q(b, R t / U, R z / U) with U = R - (x cos b + y sin b),
+ * t = -x sin b + y cos b, bilinear interpolation (zero outside the detector),
+ * scaled by pi / n_angles.  As R grows this tends to Eq. 2 applied to each
+ * detector row. */
+typedef struct fbp_fdk_plan_s *fbp_fdk_plan_t;
+
+typedef struct {
+    int n_angles, nv, nu;  /* projections [n_angles][nv][nu] */
+    double R;              /* source to rotation axis, in voxel units */
+    double du, dv;         /* detector spacing on the virtual detector */
+    int nx, ny, nz;        /* volume [nz][ny][nx], each side <= 8192 */
+} fbp_fdk_geometry;
+
+/* Plan a geometry (beta: host, n_angles radians, or NULL for a uniform full
+ * turn).  FBP_ERR_INVALID_ARG for bad sizes or a volume reaching the source
+ * circle; FBP_ERR_UNSUPPORTED beyond the FFT filter's reach (nu > 4096). */
+fbp_status fbp_fdk_plan(fbp_fdk_plan_t *out, const fbp_fdk_geometry *geometry,
+                        const double *beta, fbp_filter_type filter);
+fbp_status fbp_fdk_plan_destroy(fbp_fdk_plan_t plan);
+/* Device workspace a reconstruction needs (filtered rows and per-tile tables). */
+fbp_status fbp_fdk_workspace_bytes(fbp_fdk_plan_t plan, size_t *bytes);
+/* proj: device [n_angles][nv][nu] float; volume: device [nz][ny][nx] float;
+ * workspace: device, fbp_fdk_workspace_bytes; all 16-byte aligned.
+ * Asynchronous on `stream`; deterministic (angles summed in order per voxel). */
+fbp_status fbp_fdk_reconstruct(fbp_fdk_plan_t plan, const void *proj, void *volume,
+                               void *workspace, fbp_stream_t stream);
 
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)

@@ -64,6 +64,12 @@ class fbp_options(ctypes.Structure):
                  "tile_x", "tile_y", "angle_chunk")] + [("i0", ctypes.c_double)]
 
 
+class fbp_fdk_geometry(ctypes.Structure):
+    _fields_ = [("n_angles", ctypes.c_int), ("nv", ctypes.c_int), ("nu", ctypes.c_int),
+                ("R", ctypes.c_double), ("du", ctypes.c_double), ("dv", ctypes.c_double),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
 class fbp_tuning(ctypes.Structure):
     _fields_ = [("options", fbp_options), ("filter_ms", ctypes.c_double),
                 ("backproject_ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
@@ -98,6 +104,11 @@ _SIGS = {
     "fbp_quality": [_P, _P, _I, _I, _I, ctypes.c_double, _P, ctypes.c_size_t, _P, _P],
     "fbp_volume_from_slices": [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_double), _I,
                                ctypes.POINTER(ctypes.c_double), _I, _P, _P],
+    "fbp_fdk_plan": [ctypes.POINTER(_P), ctypes.POINTER(fbp_fdk_geometry),
+                     ctypes.POINTER(ctypes.c_double), _I],
+    "fbp_fdk_plan_destroy": [_P],
+    "fbp_fdk_workspace_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "fbp_fdk_reconstruct": [_P, _P, _P, _P, _P],
     "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
     "fbp_autotune": [_I, _I, _I, ctypes.c_double, _I, ctypes.POINTER(fbp_options), _I,
                      ctypes.POINTER(fbp_tuning)],
@@ -320,6 +331,52 @@ def volume(slices, z, z_out, out=None, stream=None):
     _check(load_library().fbp_volume_from_slices(ptrs, len(slices), zs, n, zo, len(z_out),
                                                  _ptr(out), _stream(stream)))
     return out
+
+
+class FdkPlan:
+    """FDK cone-beam plan (see fbp.h): projections [n_angles][nv][nu] on a
+    virtual detector through the axis, source radius R, volume [nz][ny][nx]."""
+
+    def __init__(self, n_angles: int, nv: int, nu: int, R: float, nx: int, ny: int, nz: int,
+                 du: float = 1.0, dv: float = 1.0, beta=None, filter: int = FBP_FILTER_RAM_LAK):
+        self.geometry = fbp_fdk_geometry(int(n_angles), int(nv), int(nu), float(R), float(du),
+                                         float(dv), int(nx), int(ny), int(nz))
+        b = None
+        if beta is not None:
+            assert len(beta) == n_angles
+            b = (ctypes.c_double * n_angles)(*[float(v) for v in beta])
+        h = _P()
+        _check(load_library().fbp_fdk_plan(ctypes.byref(h), ctypes.byref(self.geometry), b,
+                                           int(filter)))
+        self.handle = h.value
+        n = ctypes.c_size_t()
+        _check(load_library().fbp_fdk_workspace_bytes(self.handle, ctypes.byref(n)))
+        self.workspace_bytes = n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().fbp_fdk_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reconstruct(self, proj, out=None, workspace=None, stream=None):
+        import torch
+        g = self.geometry
+        assert proj.shape == (g.n_angles, g.nv, g.nu) and proj.is_contiguous()
+        assert proj.dtype == torch.float32
+        if out is None:
+            out = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device=proj.device)
+        if workspace is None:
+            workspace = torch.empty(max(self.workspace_bytes, 16), dtype=torch.uint8,
+                                    device=proj.device)
+        _check(load_library().fbp_fdk_reconstruct(self.handle, _ptr(proj), _ptr(out),
+                                                  _ptr(workspace), _stream(stream)))
+        return out
 
 
 # ------------------------------------------------------------ tensor wrapper

@@ -298,7 +298,7 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         return FBP_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (n_pix < 1 || n_pix > 16384 || n_angles < 1 || n_angles > 65535 || n_det < 1 ||
+    if (n_pix < 1 || n_pix > 16384 || n_angles < 1 || n_angles > (1 << 24) || n_det < 1 ||
         n_det > 65535) {
         set_error("fbp_plan: sizes out of range (n_pix %d, n_angles %d, n_det %d)", n_pix,
                   n_angles, n_det);

@@ -46,6 +46,8 @@ struct Plan {
     double *d_taps64;   // same in FP64
     float4 *d_fft_tw;   // FFT route: (c, c, s, s) with c + i s = exp(-2 pi i t / N), t < N
     float2 *d_fft_h;    // FFT route: (H, H), H = DFT_N of the circular taps / N (real, even)
+    const float *d_row_weight;  // FFT route, optional: [row_weight_rows][D] factors applied to
+    int row_weight_rows;        //   row r's values on load (row r uses table row r mod rows)
     int *d_status;      // device status word (0 = ok)
     TcTables *tc;       // Toeplitz route: T_hi / T_lo and their TMA maps
 };

@@ -306,7 +306,8 @@ struct FftSlice {
     int block_end;
     float i0;  // > 0: intensity input, converted on load (lambert.cuh)
     float ln_i0;
-    int pad_;
+    int wt_rows;       // > 0: row r's values are multiplied by wt[(r mod wt_rows)][j] on load
+    const float *wt;
 };
 
 template <int MAXS>
@@ -359,6 +360,24 @@ __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __gri
                 if (rows > 1) v[q].im.x = line_integral(v[q].im.x, S.i0, S.ln_i0);
                 if (rows > 2) v[q].re.y = line_integral(v[q].re.y, S.i0, S.ln_i0);
                 if (rows > 3) v[q].im.y = line_integral(v[q].im.y, S.i0, S.ln_i0);
+            }
+        }
+    }
+    if (S.wt != nullptr) {
+        // per-element weights of the row (a cone-beam cosine weight), applied to the
+        // line integrals
+        const float *w0 = S.wt + (size_t)(i0 % S.wt_rows) * D;
+        const float *w1 = S.wt + (size_t)((i0 + 1) % S.wt_rows) * D;
+        const float *w2 = S.wt + (size_t)((i0 + 2) % S.wt_rows) * D;
+        const float *w3 = S.wt + (size_t)((i0 + 3) % S.wt_rows) * D;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int j = t + q * T;
+            if (j < D) {
+                v[q].re.x *= __ldg(&w0[j]);
+                v[q].im.x *= __ldg(&w1[j]);
+                v[q].re.y *= __ldg(&w2[j]);
+                v[q].im.y *= __ldg(&w3[j]);
             }
         }
     }
@@ -425,7 +444,8 @@ FftSlice fft_slice(const Plan &p, const float *sino, int ld, void *q)
     f.block_end = 0;
     f.i0 = p.i0f;
     f.ln_i0 = p.ln_i0f;
-    f.pad_ = 0;
+    f.wt = p.d_row_weight;
+    f.wt_rows = p.row_weight_rows;
     return f;
 }
 

@@ -14,8 +14,8 @@ __global__ void radon_forward_f32_kernel(const float *__restrict__ img, float *_
                                          const double2 *__restrict__ trig, int n, int A, int D,
                                          double half_n, double half_d)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x;  // angles on x: up to 2^31 - 1 of them
     if (k >= D || i >= A) return;
     const double c = trig[i].x;  // cos / tau
     const double s = trig[i].y;  // sin / tau
@@ -56,7 +56,7 @@ __global__ void radon_forward_f32_kernel(const float *__restrict__ img, float *_
 cudaError_t launch_radon_forward_f32(const Plan &p, const float *image, float *sino,
                                      cudaStream_t s)
 {
-    dim3 grid((p.D + 127) / 128, p.A);
+    dim3 grid(p.A, (p.D + 127) / 128);
     radon_forward_f32_kernel<<<grid, 128, 0, s>>>(image, sino, p.d_trig64, p.n, p.A, p.D,
                                                  0.5 * (double)(p.n - 1),
                                                  0.5 * (double)(p.D - 1));
