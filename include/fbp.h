@@ -398,13 +398,17 @@ typedef struct {
 fbp_status fbp_fdk_plan(fbp_fdk_plan_t *out, const fbp_fdk_geometry *geometry,
                         const double *beta, fbp_filter_type filter);
 fbp_status fbp_fdk_plan_destroy(fbp_fdk_plan_t plan);
-/* Device workspace a reconstruction needs (filtered rows and per-tile tables). */
+/* Device workspace a reconstruction needs (the filtered rows; the per-tile
+ * tables belong to the plan). */
 fbp_status fbp_fdk_workspace_bytes(fbp_fdk_plan_t plan, size_t *bytes);
 /* proj: device [n_angles][nv][nu] float; volume: device [nz][ny][nx] float;
  * workspace: device, fbp_fdk_workspace_bytes; all 16-byte aligned.
  * Asynchronous on `stream`; deterministic (angles summed in order per voxel). */
 fbp_status fbp_fdk_reconstruct(fbp_fdk_plan_t plan, const void *proj, void *volume,
                                void *workspace, fbp_stream_t stream);
+/* Synchronise the device and read the plan's device status word (a bounded
+ * wait that ran out reports FBP_ERR_TIMEOUT; the word is then cleared). */
+fbp_status fbp_fdk_status(fbp_fdk_plan_t plan);
 
 /* Capacity of the scratch array behind fbp_reconstruct_static (bytes). */
 #define FBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)

@@ -109,6 +109,7 @@ _SIGS = {
     "fbp_fdk_plan_destroy": [_P],
     "fbp_fdk_workspace_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "fbp_fdk_reconstruct": [_P, _P, _P, _P, _P],
+    "fbp_fdk_status": [_P],
     "fbp_reconstruct_many": [ctypes.POINTER(_P), _I, ctypes.POINTER(fbp_batch_io), _P],
     "fbp_autotune": [_I, _I, _I, ctypes.c_double, _I, ctypes.POINTER(fbp_options), _I,
                      ctypes.POINTER(fbp_tuning)],
@@ -377,6 +378,9 @@ class FdkPlan:
         _check(load_library().fbp_fdk_reconstruct(self.handle, _ptr(proj), _ptr(out),
                                                   _ptr(workspace), _stream(stream)))
         return out
+
+    def device_status(self):
+        _check(load_library().fbp_fdk_status(self.handle))
 
 
 # ------------------------------------------------------------ tensor wrapper

@@ -107,6 +107,28 @@ bool encode_pairs_map(const Plan &p, const void *q, CUtensorMap *out)
     return true;
 }
 
+bool encode_rows_map_3d(const void *q, int row_floats, int pitch, int rows, int planes,
+                        int box_x, int box_y, CUtensorMap *out)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (enc == nullptr) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return false;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)row_floats, (cuuint64_t)rows, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4u, (cuuint64_t)pitch * 4u * (cuuint64_t)rows};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(q), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled (3D rows) failed (%d)", (int)r);
+        return false;
+    }
+    return true;
+}
+
 BpSlice slice_desc(const Plan &p, float *image)
 {
     BpSlice s;

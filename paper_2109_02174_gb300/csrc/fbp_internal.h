@@ -65,6 +65,12 @@ void set_error(const char *fmt, ...);
 // q_storage type with row stride pitch, box {2 wp, 1}.
 bool encode_pairs_map(const Plan &p, const void *q, CUtensorMap *out);
 
+// Tensor map over `planes` x `rows` rows of `row_floats` floats (row stride
+// `pitch` floats, a multiple of 4), box {box_x floats, box_y rows, 1}; outside
+// the extents TMA fills zeros.
+bool encode_rows_map_3d(const void *q, int row_floats, int pitch, int rows, int planes,
+                        int box_x, int box_y, CUtensorMap *out);
+
 // Filter launchers: write the (mid, slope) pairs of every row (see fbp.h).
 cudaError_t launch_filter_direct(const Plan &p, const float *sino, int ld, void *q,
                                  cudaStream_t s);

@@ -11,24 +11,32 @@
 //      through the FFT ramp filter, its values multiplied on load by the
 //      cosine weight R / sqrt(R^2 + u^2 + v^2) (a plan table), and leaves as
 //      (mid, slope) pairs along u;
-//   2. per (tile, angle) parameters, FP64: the projection of the tile centre,
-//      u_c = R t_c / U_c and v_c = R z_c / U_c with s_c = x_c cos b + y_c sin b,
-//      t_c = -x_c sin b + y_c cos b, U_c = R - s_c, kept as an integer detector
-//      base plus a small float offset;
-//   3. backprojection, gather-only and deterministic: one CTA per 16 x 16 x 16
-//      voxel tile, one thread per (x, y) column running down its 16 voxels.  A
-//      voxel at (dx, dy, dz) from the centre projects to
+//   2. per (tile, angle) parameters, computed once per plan in FP64: the
+//      projection of the tile centre, u_c = R t_c / U_c and v_c = R z_c / U_c
+//      (s_c = x_c cos b + y_c sin b, t_c = -x_c sin b + y_c cos b,
+//      U_c = R - s_c), and the detector window the tile's eight corners span
+//      (a perspective projection maps the box into the hull of their images),
+//      stored as the window's first pair and row plus the centre's offset from
+//      them;
+//   3. backprojection, gather-only and deterministic: one CTA per
+//      16 x 16 x 16 voxel tile.  A producer warp brings each angle's window of
+//      filtered pairs into shared memory with one 3D TMA load (rows outside
+//      the detector arrive as zeros) into a ring of stages; 256 consumer
+//      threads, one per (x, y) column, run down their 16 voxels.  A voxel at
+//      (dx, dy, dz) from the centre projects to
 //          u - u_c = R (dt U_c + t_c ds) / (U U_c),  v - v_c = R (dz U_c + z_c ds) / (U U_c)
-//      (ds = dx cos b + dy sin b, dt = -dx sin b + dy cos b, U = U_c - ds), all
-//      small offsets, so FP32 keeps the detector position to about 1e-6 bins;
-//      the u sample and the weight (R/U)^2 are formed once per column and
-//      angle, then each voxel reads two rows of pairs (bilinear) and adds in
-//      angle order; the sum is scaled by pi / A (a full turn).
+//      (ds = dx cos b + dy sin b, dt = -dx sin b + dy cos b, U = U_c - ds), small
+//      offsets, so FP32 keeps the detector position to about 1e-6 bins; the u
+//      sample and the weight (R/U)^2 are formed once per column and angle,
+//      each voxel reads two rows of pairs (bilinear), and angles are summed in
+//      order; the sum is scaled by pi / A (a full turn).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "fbp_internal.h"
+#include "ptx.cuh"
 
 namespace fbp {
 
@@ -36,33 +44,63 @@ cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q,
 
 namespace {
 
-constexpr int kT = 16;  // tile edge (voxels)
+constexpr int kT = 16;                 // tile edge (voxels)
+constexpr int kConsumers = kT * kT;    // one thread per (x, y) column
+constexpr int kConsumerWarps = kConsumers / 32;
+constexpr int kThreads = kConsumers + 32;  // + the TMA producer warp
+constexpr int kStages = 2;
+constexpr size_t kSmemBudget = 200 * 1024;
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: x + kMagic holds round(x) in its low bits
+constexpr int kMagicLow = 0x4B400000;
+
+struct FdkPrm {
+    float c, s, uc, tc;  // cos b, sin b, U_c, t_c
+    float kuo, kvo;      // centre's bin and row coordinate, relative to the window
+    int p0, r0;          // window's first pair (even) and first row
+};
 
 struct FdkPlan {
     int A, nv, nu, nx, ny, nz;
     double R, du, dv;
     int tiles_x, tiles_y, tiles_z;
-    fbp_plan_t filt;   // FFT filter plan over the A nv rows
-    float *d_wt;       // [nv][nu] cosine weights
-    double2 *d_trig;   // (cos b, sin b)
+    int wu, wv;          // window: pairs (even) and rows of one angle's box
+    int ch;              // angles per shared-memory stage
+    size_t box_bytes;    // one angle's box in shared memory (128-byte multiple)
+    fbp_plan_t filt;     // FFT filter plan over the A nv rows
+    float *d_wt;         // [nv][nu] cosine weights
+    double2 *d_trig;     // (cos b, sin b)
+    FdkPrm *d_prm;       // [tiles][A]
     int device;
-};
-
-struct FdkPrm {
-    float c, s, uc, tc;  // cos b, sin b, U_c, t_c
-    float kuo, kvo;      // centre's detector column / row minus the integer bases
-    int kub, kvb;        // integer bases (bin index, row index)
 };
 
 struct FdkArgs {
     int A, nv, nu, nx, ny, nz, pitch2, tiles_x, tiles_y, tiles_z;
+    int wu, wv, ch, box_bytes;
     float Ru, Rv, R;  // R / du, R / dv, R
     double R64, du, dv;
     float scale;      // pi / A
+    int *status;
 };
 
+__device__ __forceinline__ double ku_of(const FdkArgs &g, double x, double y, double cb,
+                                        double sb)
+{
+    const double t = -x * sb + y * cb, U = g.R64 - (x * cb + y * sb);
+    return g.R64 * t / U / g.du + 0.5 * (g.nu - 1);
+}
+
+__device__ __forceinline__ double kv_of(const FdkArgs &g, double x, double y, double z,
+                                        double cb, double sb)
+{
+    const double U = g.R64 - (x * cb + y * sb);
+    return g.R64 * z / U / g.dv + 0.5 * (g.nv - 1);
+}
+
+// Parameters of every (tile, angle) and the largest window any needs
+// (ext[0]: pairs, ext[1]: rows).
 __global__ void __launch_bounds__(256)
-    fdk_params_kernel(const double2 *__restrict__ trig, FdkPrm *__restrict__ prm, FdkArgs g)
+    fdk_params_kernel(const double2 *__restrict__ trig, FdkPrm *__restrict__ prm, FdkArgs g,
+                      int *ext)
 {
     const long ntile = (long)g.tiles_x * g.tiles_y * g.tiles_z;
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,43 +110,94 @@ __global__ void __launch_bounds__(256)
     const int tx = (int)(tile % g.tiles_x);
     const int ty = (int)((tile / g.tiles_x) % g.tiles_y);
     const int tz = (int)(tile / ((long)g.tiles_x * g.tiles_y));
-    const double xc = (double)(tx * kT) + 0.5 * (kT - 1) - 0.5 * (g.nx - 1);
-    const double yc = (double)(ty * kT) + 0.5 * (kT - 1) - 0.5 * (g.ny - 1);
-    const double zc = (double)(tz * kT) + 0.5 * (kT - 1) - 0.5 * (g.nz - 1);
+    const double h = 0.5 * (kT - 1);
+    const double xc = (double)(tx * kT) + h - 0.5 * (g.nx - 1);
+    const double yc = (double)(ty * kT) + h - 0.5 * (g.ny - 1);
+    const double zc = (double)(tz * kT) + h - 0.5 * (g.nz - 1);
     const double2 cs = trig[a];
+    double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+    for (int k = 0; k < 8; ++k) {
+        const double x = xc + ((k & 1) ? h : -h), y = yc + ((k & 2) ? h : -h);
+        const double z = zc + ((k & 4) ? h : -h);
+        const double ku = ku_of(g, x, y, cs.x, cs.y), kv = kv_of(g, x, y, z, cs.x, cs.y);
+        umin = fmin(umin, ku);
+        umax = fmax(umax, ku);
+        vmin = fmin(vmin, kv);
+        vmax = fmax(vmax, kv);
+    }
+    // bins floor(umin) .. floor(umax) use pairs floor(umin)+1 .. floor(umax)+1; one
+    // pair of margin each side, first pair even (16-byte TMA coordinate)
+    const int p0 = (int)floor(umin) & ~1;
+    const int p_last = (int)floor(umax) + 2;
+    // rows floor(vmin) .. floor(vmax)+1, one row of margin each side
+    const int r0 = (int)floor(vmin) - 1;
+    const int r_last = (int)floor(vmax) + 2;
+    atomicMax(&ext[0], p_last - p0 + 1);
+    atomicMax(&ext[1], r_last - r0 + 1);
     const double sc = xc * cs.x + yc * cs.y;
     const double tc = -xc * cs.y + yc * cs.x;
     const double Uc = g.R64 - sc;
-    const double ku = g.R64 * tc / Uc / g.du + 0.5 * (g.nu - 1);
-    const double kv = g.R64 * zc / Uc / g.dv + 0.5 * (g.nv - 1);
-    const double fu = floor(ku), fv = floor(kv);
     FdkPrm P;
     P.c = (float)cs.x;
     P.s = (float)cs.y;
     P.uc = (float)Uc;
     P.tc = (float)tc;
-    P.kuo = (float)(ku - fu);
-    P.kvo = (float)(kv - fv);
-    P.kub = (int)fu;
-    P.kvb = (int)fv;
+    P.kuo = (float)(ku_of(g, xc, yc, cs.x, cs.y) - (double)(p0 - 1));  // bin (p0-1) <-> window pair 0
+    P.kvo = (float)(kv_of(g, xc, yc, zc, cs.x, cs.y) - (double)r0);
+    P.p0 = p0;
+    P.r0 = r0;
     prm[idx] = P;
 }
 
-// Pair (mid, slope) of bin `bin` of one detector row, interpolated at offset w
-// in [-1/2, 1/2) from the bin's interval centre; zero outside the detector.
-__device__ __forceinline__ float sample(const float2 *__restrict__ row, int pair, int npairs,
-                                        float w)
+__global__ void __launch_bounds__(kThreads)
+    fdk_backproject_kernel(const __grid_constant__ CUtensorMap qmap,
+                           const FdkPrm *__restrict__ prm, float *__restrict__ vol,
+                           const FdkArgs g)
 {
-    if (pair < 0 || pair >= npairs) return 0.0f;
-    const float2 m = __ldg(&row[pair]);
-    return fmaf(w, m.y, m.x);
-}
-
-__global__ void __launch_bounds__(kT * kT)
-    fdk_backproject_kernel(const float2 *__restrict__ q, const FdkPrm *__restrict__ prm,
-                           float *__restrict__ vol, FdkArgs g)
-{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t base = (smem_addr(smem) + 127u) & ~127u;
+    unsigned char *bp = smem + (base - smem_addr(smem));
+    const uint32_t full0 = base + (uint32_t)(kStages * g.ch * g.box_bytes);
+    const uint32_t empty0 = full0 + 8u * kStages;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full0 + 8u * s, 1);
+            mbar_init(empty0 + 8u * s, kConsumerWarps);
+        }
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
     const int tile = blockIdx.x;
+    const FdkPrm *pt = prm + (size_t)tile * g.A;
+    const int nch = (g.A + g.ch - 1) / g.ch;
+    const uint32_t box_payload = (uint32_t)(g.wv * 2 * g.wu * 4);
+
+    if (warp == kConsumerWarps) {
+        // ---------------------------------------------------- TMA producer
+        for (int c = 0; c < nch; ++c) {
+            const int s = c % kStages;
+            const uint32_t use = (uint32_t)(c / kStages);
+            bool ok = true;
+            if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * s, (use - 1) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *reinterpret_cast<volatile int *>(g.status) = FBP_ERR_TIMEOUT;
+                return;
+            }
+            const int a0 = c * g.ch;
+            const int na = min(g.ch, g.A - a0);
+            if (lane == 0) mbar_arrive_expect_tx(full0 + 8u * s, (uint32_t)na * box_payload);
+            __syncwarp();
+            if (lane < na) {
+                const FdkPrm P = pt[a0 + lane];
+                tma_load_3d(base + (uint32_t)((s * g.ch + lane) * g.box_bytes), &qmap, 2 * P.p0,
+                            P.r0, a0 + lane, full0 + 8u * s);
+            }
+        }
+        return;
+    }
+
+    // -------------------------------------------------------- consumers
     const int tx = tile % g.tiles_x;
     const int ty = (tile / g.tiles_x) % g.tiles_y;
     const int tz = tile / (g.tiles_x * g.tiles_y);
@@ -119,37 +208,51 @@ __global__ void __launch_bounds__(kT * kT)
     float acc[kT];
 #pragma unroll
     for (int j = 0; j < kT; ++j) acc[j] = 0.0f;
-    const FdkPrm *pt = prm + (size_t)tile * g.A;
-    const size_t plane = (size_t)g.nv * g.pitch2;
-    for (int a = 0; a < g.A; ++a) {
-        const FdkPrm P = pt[a];
-        const float ds = fmaf(dx, P.c, dy * P.s);
-        const float dt = fmaf(dy, P.c, -dx * P.s);
-        const float U = P.uc - ds;
-        const float inv = 1.0f / (U * P.uc);
-        const float ku = fmaf(g.Ru * fmaf(dt, P.uc, P.tc * ds), inv, P.kuo);
-        const float fk = floorf(ku);
-        const int pair = P.kub + (int)fk + 1;  // pair of the interval [bin, bin + 1]
-        const float wu = ku - fk - 0.5f;
-        const float rU = g.R * P.uc * inv;     // R / U
-        const float W = rU * rU;
-        const float bz = g.Rv * P.uc * inv;    // d(row) / d(dz)
-        const float v0 = fmaf(g.Rv * zc * ds, inv, P.kvo);
-        const float2 *qa = q + (size_t)a * plane;
-#pragma unroll
-        for (int j = 0; j < kT; ++j) {
-            const float kv = fmaf((float)j - 0.5f * (kT - 1), bz, v0);
-            const float fv = floorf(kv);
-            const int i = P.kvb + (int)fv;
-            const float wv = kv - fv;
-            const float r0 = (i >= 0 && i < g.nv)
-                                 ? sample(qa + (size_t)i * g.pitch2, pair, g.pitch2, wu)
-                                 : 0.0f;
-            const float r1 = (i + 1 >= 0 && i + 1 < g.nv)
-                                 ? sample(qa + (size_t)(i + 1) * g.pitch2, pair, g.pitch2, wu)
-                                 : 0.0f;
-            acc[j] = fmaf(W, fmaf(wv, r1 - r0, r0), acc[j]);
+    const int wu = g.wu, wv = g.wv;
+    for (int c = 0; c < nch; ++c) {
+        const int s = c % kStages;
+        const bool ok = mbar_wait_bounded(full0 + 8u * s, (uint32_t)(c / kStages) & 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) *reinterpret_cast<volatile int *>(g.status) = FBP_ERR_TIMEOUT;
+            return;
         }
+        const int a0 = c * g.ch;
+        const int na = min(g.ch, g.A - a0);
+        for (int k = 0; k < na; ++k) {
+            const FdkPrm P = pt[a0 + k];
+            const float ds = fmaf(dx, P.c, dy * P.s);
+            const float dt = fmaf(dy, P.c, -dx * P.s);
+            const float U = P.uc - ds;
+            const float inv = 1.0f / (U * P.uc);
+            const float ku = fmaf(g.Ru * fmaf(dt, P.uc, P.tc * ds), inv, P.kuo);
+            const float fk = floorf(ku);
+            // window pair of the voxel's interval; kept inside the window
+            const int b = min(max((int)fk, 0), wu - 1);
+            const float wu_off = ku - fk - 0.5f;
+            const float rU = g.R * P.uc * inv;  // R / U
+            const float W = rU * rU;
+            const float bz = g.Rv * P.uc * inv;  // d(row) / d(dz)
+            const float v0 = fmaf(g.Rv * zc * ds, inv, P.kvo) - 0.5f;
+            const float2 *win =
+                reinterpret_cast<const float2 *>(bp + (size_t)(s * g.ch + k) * g.box_bytes) + b;
+#pragma unroll
+            for (int j = 0; j < kT; ++j) {
+                const float kvh = fmaf((float)j - 0.5f * (kT - 1), bz, v0);  // kv - 1/2
+                const float t = kvh + kMagic;
+                const int fl = __float_as_int(t) - kMagicLow;  // floor(kv)
+                const float wv_off = kvh - (t - kMagic) + 0.5f;  // kv - floor(kv)
+                const int r = min(max(fl, 0), wv - 2);          // rows r, r+1 of the window
+                const float2 m0 = win[r * wu];
+                const float2 m1 = win[(r + 1) * wu];
+                const float q0 = fmaf(wu_off, m0.y, m0.x);
+                const float q1 = fmaf(wu_off, m1.y, m1.x);
+                acc[j] = fmaf(W, fmaf(wv_off, q1 - q0, q0), acc[j]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty0 + 8u * s)
+                         : "memory");
     }
     const int ix = tx * kT + cx, iy = ty * kT + cy;
     if (ix < g.nx && iy < g.ny) {
@@ -169,9 +272,39 @@ size_t q_bytes(const FdkPlan &f)
     return al256(sizeof(float) * (size_t)f.A * f.nv * (size_t)p->pitch);
 }
 
-size_t prm_bytes(const FdkPlan &f)
+size_t bp_smem_bytes(const FdkPlan &f)
 {
-    return al256(sizeof(FdkPrm) * (size_t)f.tiles_x * f.tiles_y * f.tiles_z * (size_t)f.A);
+    return 128 + (size_t)kStages * f.ch * f.box_bytes + 16 * kStages;
+}
+
+FdkArgs args_of(const FdkPlan &f)
+{
+    const Plan &p = *reinterpret_cast<const Plan *>(f.filt);
+    FdkArgs g;
+    std::memset(&g, 0, sizeof g);
+    g.A = f.A;
+    g.nv = f.nv;
+    g.nu = f.nu;
+    g.nx = f.nx;
+    g.ny = f.ny;
+    g.nz = f.nz;
+    g.pitch2 = p.pitch / 2;
+    g.tiles_x = f.tiles_x;
+    g.tiles_y = f.tiles_y;
+    g.tiles_z = f.tiles_z;
+    g.wu = f.wu;
+    g.wv = f.wv;
+    g.ch = f.ch;
+    g.box_bytes = (int)f.box_bytes;
+    g.Ru = (float)(f.R / f.du);
+    g.Rv = (float)(f.R / f.dv);
+    g.R = (float)f.R;
+    g.R64 = f.R;
+    g.du = f.du;
+    g.dv = f.dv;
+    g.scale = (float)(M_PI / (double)f.A);
+    g.status = p.d_status;
+    return g;
 }
 
 void free_fdk(FdkPlan *f)
@@ -180,6 +313,7 @@ void free_fdk(FdkPlan *f)
     if (f->filt) fbp_plan_destroy(f->filt);
     cudaFree(f->d_wt);
     cudaFree(f->d_trig);
+    cudaFree(f->d_prm);
     delete f;
 }
 
@@ -201,12 +335,13 @@ fbp_status fbp_fdk_plan(fbp_fdk_plan_t *out, const fbp_fdk_geometry *geo, const 
     const fbp_fdk_geometry g = *geo;
     if (g.n_angles < 1 || g.nv < 1 || g.nu < 1 || g.nx < 1 || g.ny < 1 || g.nz < 1 ||
         !std::isfinite(g.R) || !std::isfinite(g.du) || !std::isfinite(g.dv) || !(g.du > 0.0) ||
-        !(g.dv > 0.0) || g.nx > 8192 || g.ny > 8192 || g.nz > 8192) {
+        !(g.dv > 0.0) || g.nx > 8192 || g.ny > 8192 || g.nz > 8192 || g.n_angles > (1 << 20)) {
         set_error("fbp_fdk_plan: sizes must be >= 1 (volume <= 8192 a side), spacings > 0");
         return FBP_ERR_INVALID_ARG;
     }
-    const double rmax = std::sqrt(0.25 * (g.nx - 1.0) * (g.nx - 1.0) +
-                                  0.25 * (g.ny - 1.0) * (g.ny - 1.0));
+    // every voxel of every tile (tiles may overhang the volume) inside the source circle
+    const double hx = 0.5 * (g.nx - 1) + kT, hy = 0.5 * (g.ny - 1) + kT;
+    const double rmax = std::sqrt(hx * hx + hy * hy);
     if (!(g.R > rmax + 1.0)) {
         set_error("fbp_fdk_plan: the source radius %g must exceed the volume's reach %g + 1",
                   g.R, rmax);
@@ -253,17 +388,47 @@ fbp_status fbp_fdk_plan(fbp_fdk_plan_t *out, const fbp_fdk_geometry *geo, const 
         const double b = beta ? beta[a] : 2.0 * M_PI * a / g.n_angles;
         trig[(size_t)a] = make_double2(std::cos(b), std::sin(b));
     }
+    const size_t nprm = (size_t)f->tiles_x * f->tiles_y * f->tiles_z * (size_t)g.n_angles;
+    int *d_ext = nullptr;
+    int ext[2] = {0, 0};
     cudaError_t e = cudaMalloc(&f->d_wt, sizeof(float) * wt.size());
     if (e == cudaSuccess) e = cudaMalloc(&f->d_trig, sizeof(double2) * trig.size());
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_prm, sizeof(FdkPrm) * nprm);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ext, sizeof ext);
     if (e == cudaSuccess)
         e = cudaMemcpy(f->d_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(f->d_trig, trig.data(), sizeof(double2) * trig.size(),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_ext, ext, sizeof ext, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const FdkArgs a = args_of(*f);
+        fdk_params_kernel<<<(unsigned)((nprm + 255) / 256), 256>>>(f->d_trig, f->d_prm, a, d_ext);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ext, d_ext, sizeof ext, cudaMemcpyDeviceToHost);
+    cudaFree(d_ext);
     if (e != cudaSuccess) {
         free_fdk(f);
         set_error("fbp_fdk_plan: %s", cudaGetErrorString(e));
         return FBP_ERR_OUT_OF_MEMORY;
+    }
+    f->wu = (ext[0] + 1) & ~1;  // even: the box's row of pairs is a multiple of 16 bytes
+    f->wv = std::max(ext[1], 2);
+    f->box_bytes = ((size_t)f->wv * 2 * f->wu * 4 + 127) & ~(size_t)127;
+    if (2 * f->wu > 256 || f->wv > 256) {
+        free_fdk(f);
+        set_error("fbp_fdk_plan: a tile's detector window (%d pairs x %d rows) exceeds one TMA "
+                  "box (128 x 256)", ext[0], ext[1]);
+        return FBP_ERR_UNSUPPORTED;
+    }
+    f->ch = 8;
+    while (f->ch > 1 && bp_smem_bytes(*f) > kSmemBudget) f->ch /= 2;
+    if (bp_smem_bytes(*f) > kSmemBudget) {
+        free_fdk(f);
+        set_error("fbp_fdk_plan: a tile's detector window (%zu bytes) does not fit shared memory",
+                  f->box_bytes);
+        return FBP_ERR_UNSUPPORTED;
     }
     Plan *p = reinterpret_cast<Plan *>(f->filt);
     p->d_row_weight = f->d_wt;
@@ -285,7 +450,7 @@ fbp_status fbp_fdk_workspace_bytes(fbp_fdk_plan_t plan, size_t *bytes)
         set_error("fbp_fdk_workspace_bytes: NULL argument");
         return FBP_ERR_INVALID_ARG;
     }
-    *bytes = q_bytes(*f) + prm_bytes(*f);
+    *bytes = q_bytes(*f);
     return FBP_OK;
 }
 
@@ -304,37 +469,20 @@ fbp_status fbp_fdk_reconstruct(fbp_fdk_plan_t plan, const void *proj, void *volu
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const Plan &p = *reinterpret_cast<const Plan *>(f->filt);
-    unsigned char *ws = static_cast<unsigned char *>(workspace);
-    float *q = reinterpret_cast<float *>(ws);
-    FdkPrm *prm = reinterpret_cast<FdkPrm *>(ws + q_bytes(*f));
+    float *q = static_cast<float *>(workspace);
+    CUtensorMap qmap;
+    if (!encode_rows_map_3d(q, 2 * (f->nu + 1), p.pitch, f->nv, f->A, 2 * f->wu, f->wv, &qmap))
+        return FBP_ERR_CUDA;
     cudaError_t e = launch_filter_fft(p, static_cast<const float *>(proj), f->nu, q, s);
-    FdkArgs g;
-    g.A = f->A;
-    g.nv = f->nv;
-    g.nu = f->nu;
-    g.nx = f->nx;
-    g.ny = f->ny;
-    g.nz = f->nz;
-    g.pitch2 = p.pitch / 2;
-    g.tiles_x = f->tiles_x;
-    g.tiles_y = f->tiles_y;
-    g.tiles_z = f->tiles_z;
-    g.Ru = (float)(f->R / f->du);
-    g.Rv = (float)(f->R / f->dv);
-    g.R = (float)f->R;
-    g.R64 = f->R;
-    g.du = f->du;
-    g.dv = f->dv;
-    g.scale = (float)(M_PI / (double)f->A);
-    const long ntile = (long)f->tiles_x * f->tiles_y * f->tiles_z;
+    const FdkArgs g = args_of(*f);
+    const size_t smem = bp_smem_bytes(*f);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fdk_backproject_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        const long work = ntile * f->A;
-        fdk_params_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(f->d_trig, prm, g);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        fdk_backproject_kernel<<<(unsigned)ntile, kT * kT, 0, s>>>(
-            reinterpret_cast<const float2 *>(q), prm, static_cast<float *>(volume), g);
+        const unsigned ntile = (unsigned)(f->tiles_x * f->tiles_y * f->tiles_z);
+        fdk_backproject_kernel<<<ntile, kThreads, smem, s>>>(qmap, f->d_prm,
+                                                             static_cast<float *>(volume), g);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
@@ -342,6 +490,16 @@ fbp_status fbp_fdk_reconstruct(fbp_fdk_plan_t plan, const void *proj, void *volu
         return FBP_ERR_CUDA;
     }
     return FBP_OK;
+}
+
+fbp_status fbp_fdk_status(fbp_fdk_plan_t plan)
+{
+    const FdkPlan *f = reinterpret_cast<const FdkPlan *>(plan);
+    if (f == nullptr) {
+        set_error("fbp_fdk_status: NULL plan");
+        return FBP_ERR_INVALID_ARG;
+    }
+    return fbp_device_status(f->filt);
 }
 
 }  // extern "C"

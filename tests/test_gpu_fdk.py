@@ -31,6 +31,7 @@ def _run(fbp, P, beta, R, du, dv, kind, nx, ny, nz, give_beta=True):
                        beta=beta if give_beta else None, filter=kind)
     vol = plan.reconstruct(torch.from_numpy(P.astype(np.float32)).cuda())
     torch.cuda.synchronize()
+    plan.device_status()
     ref = oracle.fdk(P.astype(np.float32).astype(np.float64), beta, R, du, dv, kind, nx, ny, nz,
                      nthreads=16)
     return vol.cpu().numpy().astype(np.float64), ref, plan
