@@ -399,8 +399,15 @@ def run_configs(fbp):
     torch.cuda.synchronize()
     fms = _timed_flushed(lambda: fdk_plan.reconstruct(proj, fvol, fws), 3, stream, flush)
     fupd = 256 ** 3 * 360
-    out["fdk_256cubed_360x320x448"] = {"ms": fms, "voxel_updates_per_s": fupd / (fms / 1e3),
-                                       "gupdates_per_s": fupd / (fms / 1e3) / 1e9}
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks()[0].get("sm_max_mhz", 2070.0))
+    smem_ceiling = 8 * sms * mhz / 1e3  # two 8-byte shared loads per update: 8 updates/clk/SM
+    out["fdk_256cubed_360x320x448"] = {
+        "ms": fms, "voxel_updates_per_s": fupd / (fms / 1e3),
+        "gupdates_per_s": fupd / (fms / 1e3) / 1e9,
+        "smem_ceiling_gupdates_per_s": smem_ceiling,
+        "frac_of_smem_ceiling": fupd / (fms / 1e3) / 1e9 / smem_ceiling,
+        "what": "weight + FFT filter of 115200 rows + TMA-staged backprojection"}
     fdk_plan.close()
     # a volume from a stack of 64 reconstructed 512^2 slices, four planes per
     # gap (253 planes): an HBM-bound stream; minimal bytes = slices read once
