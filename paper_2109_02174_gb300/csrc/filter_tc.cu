@@ -182,6 +182,10 @@ struct TcArgs {
     int *status;
 };
 
+// INTENSITY: the sinogram holds intensities (plan option i0), converted when
+// the loaders split them; a separate instantiation, since the kernel sits at
+// its register limit and the plain path should not pay for the conversion.
+template <bool INTENSITY>
 __global__ void __launch_bounds__(kThreads, 1)
     filter_tc_kernel(const __grid_constant__ CUtensorMap t_hi, const __grid_constant__ CUtensorMap t_lo,
                      const TcArgs args)
@@ -348,8 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int r = cw * kRowsPerLoader + i;
                 float x = cur[i];
                 // intensities: converted here, a chunk after their loads were issued
-                if (args.i0 > 0.0f && m0 + r < args.A && kc * kBK + lane < args.D)
-                    x = line_integral(x, args.i0, args.ln_i0);
+                if constexpr (INTENSITY)
+                    if (m0 + r < args.A && kc * kBK + lane < args.D)
+                        x = line_integral(x, args.i0, args.ln_i0);
                 const uint32_t hi = tf32_rna(x);
                 const uint32_t lo = tf32_rna(x - __uint_as_float(hi));
                 // 128-byte swizzle: 16-byte chunk (lane / 4) XOR (row mod 8)
@@ -398,7 +403,8 @@ cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, cons
                                   float *const *qs, int n, cudaStream_t s)
 {
     const size_t smem = filter_tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(filter_tc_kernel,
+    const bool intensity = p.i0 > 0.0;
+    cudaError_t e = cudaFuncSetAttribute(intensity ? filter_tc_kernel<true> : filter_tc_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int b = 0; b < n; b += kTcMaxSlices) {
@@ -419,7 +425,10 @@ cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, cons
         a.ln_i0 = p.ln_i0f;
         a.status = p.d_status;
         dim3 grid((p.pitch / 2 + kStep - 1) / kStep, a.m_tiles * cnt);
-        filter_tc_kernel<<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);
+        if (intensity)
+            filter_tc_kernel<true><<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);
+        else
+            filter_tc_kernel<false><<<grid, kThreads, smem, s>>>(p.tc->t_hi, p.tc->t_lo, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
