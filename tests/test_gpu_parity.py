@@ -412,3 +412,27 @@ def test_misaligned_and_null_buffers_are_rejected(fbp):
         fbp.fbp_filter(plan.handle, q.data_ptr(), 10, img.data_ptr(), 0)
     assert e.value.status == fbp.FBP_ERR_INVALID_ARG
     plan.device_status()
+
+
+def test_maximum_sizes_direct_route(fbp):
+    """An 8192^2 image with 11587 bins: beyond the FFT route's reach (2 n_det - 1
+    > 8192), so the plan takes the direct filter; sampled pixels (and a full
+    row through the centre) against the oracle."""
+    import torch
+    n, A = 8192, 8
+    D = synthetic.det_for(n)
+    spec = synthetic.SliceSpec(n, A, D, 6, seed=81, filter=0)
+    th = synthetic.default_angles(A)
+    sino = synthetic.sinogram(spec, th).astype(np.float32)
+    plan = fbp.Plan(n, A, D)
+    assert plan.filter_path == fbp.FBP_PATH_DIRECT
+    img = plan.reconstruct(torch.from_numpy(sino).cuda())
+    torch.cuda.synchronize()
+    plan.device_status()
+    Q = oracle.filter_rows(sino.astype(np.float64), 0, 1.0, nthreads=NTHREADS)
+    rng = np.random.default_rng(81)
+    rows = np.concatenate([rng.integers(0, n, 400), np.full(512, n // 2)])
+    cols = np.concatenate([rng.integers(0, n, 400), np.arange(0, n, 16)])
+    ref = oracle.backproject_pixels(Q, th, 1.0, n, rows, cols)
+    got = img[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
+    assert_parity(got.astype(np.float64), ref)
