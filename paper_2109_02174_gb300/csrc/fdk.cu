@@ -28,8 +28,9 @@
 //      (ds = dx cos b + dy sin b, dt = -dx sin b + dy cos b, U = U_c - ds), small
 //      offsets, so FP32 keeps the detector position to about 1e-6 bins; the u
 //      sample and the weight (R/U)^2 are formed once per column and angle,
-//      each voxel reads two rows of pairs (bilinear), and angles are summed in
-//      order; the sum is scaled by pi / A (a full turn).
+//      each voxel reads two rows of pairs (bilinear; voxels taken two at a time
+//      in packed f32x2 arithmetic), and angles are summed in order; the sum is
+//      scaled by pi / A (a full turn).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256)
     prm[idx] = P;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
     fdk_backproject_kernel(const __grid_constant__ CUtensorMap qmap,
                            const FdkPrm *__restrict__ prm, float *__restrict__ vol,
                            const FdkArgs g)
@@ -205,10 +206,13 @@ __global__ void __launch_bounds__(kThreads)
     const float dx = (float)cx - 0.5f * (kT - 1);  // exact
     const float dy = (float)cy - 0.5f * (kT - 1);
     const float zc = (float)((double)(tz * kT) + 0.5 * (kT - 1) - 0.5 * (g.nz - 1));
-    float acc[kT];
+    // voxels j and j + 1 of the column run as one packed f32x2 pair
+    float2 acc[kT / 2];
 #pragma unroll
-    for (int j = 0; j < kT; ++j) acc[j] = 0.0f;
+    for (int jj = 0; jj < kT / 2; ++jj) acc[jj] = make_float2(0.0f, 0.0f);
     const int wu = g.wu, wv = g.wv;
+    const float2 kM2 = make_float2(kMagic, kMagic), kNegM2 = make_float2(-kMagic, -kMagic);
+    const float2 kNeg1 = make_float2(-1.0f, -1.0f), kHalf2 = make_float2(0.5f, 0.5f);
     for (int c = 0; c < nch; ++c) {
         const int s = c % kStages;
         const bool ok = mbar_wait_bounded(full0 + 8u * s, (uint32_t)(c / kStages) & 1u);
@@ -233,20 +237,27 @@ __global__ void __launch_bounds__(kThreads)
             const float W = rU * rU;
             const float bz = g.Rv * P.uc * inv;  // d(row) / d(dz)
             const float v0 = fmaf(g.Rv * zc * ds, inv, P.kvo) - 0.5f;
+            const float2 bz2 = make_float2(bz, bz), v02 = make_float2(v0, v0);
+            const float2 W2 = make_float2(W, W);
             const float2 *win =
                 reinterpret_cast<const float2 *>(bp + (size_t)(s * g.ch + k) * g.box_bytes) + b;
 #pragma unroll
-            for (int j = 0; j < kT; ++j) {
-                const float kvh = fmaf((float)j - 0.5f * (kT - 1), bz, v0);  // kv - 1/2
-                const float t = kvh + kMagic;
-                const int fl = __float_as_int(t) - kMagicLow;  // floor(kv)
-                const float wv_off = kvh - (t - kMagic) + 0.5f;  // kv - floor(kv)
-                const int r = min(max(fl, 0), wv - 2);          // rows r, r+1 of the window
-                const float2 m0 = win[r * wu];
-                const float2 m1 = win[(r + 1) * wu];
-                const float q0 = fmaf(wu_off, m0.y, m0.x);
-                const float q1 = fmaf(wu_off, m1.y, m1.x);
-                acc[j] = fmaf(W, fmaf(wv_off, q1 - q0, q0), acc[j]);
+            for (int jj = 0; jj < kT / 2; ++jj) {
+                const float2 dz = make_float2((float)(2 * jj) - 0.5f * (kT - 1),
+                                              (float)(2 * jj + 1) - 0.5f * (kT - 1));
+                const float2 kvh = __ffma2_rn(dz, bz2, v02);  // kv - 1/2
+                const float2 t = __fadd2_rn(kvh, kM2);
+                const float2 fl_f = __fadd2_rn(t, kNegM2);   // floor(kv), as floats
+                // kv - floor(kv) = (kvh - floor) + 1/2
+                const float2 wv_off = __fadd2_rn(__ffma2_rn(fl_f, kNeg1, kvh), kHalf2);
+                const int r0 = min(max(__float_as_int(t.x) - kMagicLow, 0), wv - 2);
+                const int r1 = min(max(__float_as_int(t.y) - kMagicLow, 0), wv - 2);
+                const float2 m00 = win[r0 * wu], m01 = win[(r0 + 1) * wu];
+                const float2 m10 = win[r1 * wu], m11 = win[(r1 + 1) * wu];
+                const float2 q0 = make_float2(fmaf(wu_off, m00.y, m00.x), fmaf(wu_off, m10.y, m10.x));
+                const float2 q1 = make_float2(fmaf(wu_off, m01.y, m01.x), fmaf(wu_off, m11.y, m11.x));
+                const float2 d = __ffma2_rn(q0, kNeg1, q1);   // q1 - q0
+                acc[jj] = __ffma2_rn(W2, __ffma2_rn(wv_off, d, q0), acc[jj]);
             }
         }
         __syncwarp();
@@ -259,7 +270,9 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int j = 0; j < kT; ++j) {
             const int iz = tz * kT + j;
-            if (iz < g.nz) vol[((size_t)iz * g.ny + iy) * g.nx + ix] = acc[j] * g.scale;
+            if (iz < g.nz)
+                vol[((size_t)iz * g.ny + iy) * g.nx + ix] =
+                    ((j & 1) ? acc[j / 2].y : acc[j / 2].x) * g.scale;
         }
     }
 }
@@ -466,6 +479,12 @@ fbp_status fbp_fdk_reconstruct(fbp_fdk_plan_t plan, const void *proj, void *volu
           reinterpret_cast<uintptr_t>(workspace)) & 15u) != 0) {
         set_error("fbp_fdk_reconstruct: buffers must be 16-byte aligned");
         return FBP_ERR_ALIGNMENT;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != f->device) {
+        set_error("fbp_fdk_reconstruct: plan was made on device %d, current device is %d",
+                  f->device, dev);
+        return FBP_ERR_INVALID_ARG;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const Plan &p = *reinterpret_cast<const Plan *>(f->filt);
