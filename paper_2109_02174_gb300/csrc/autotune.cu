@@ -25,7 +25,7 @@
 
 namespace fbp {
 cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
-                         int *status, cudaStream_t s);
+                         int *status, cudaStream_t s, int *sched, int n_sched);
 }  // namespace fbp
 
 using namespace fbp;
@@ -97,15 +97,23 @@ double time_parts(const Plan *p, const std::vector<fbp_batch_io> &io, int parts,
 {
     const int batch = (int)io.size();
     std::vector<const Plan *> ps((size_t)batch, p);
-    if (enqueue_many(ps.data(), io.data(), batch, parts, p->d_status, s) != cudaSuccess)
+    // work counters as a batch has them (dynamic item hand-out)
+    constexpr int kCounters = 16;
+    int *sched = nullptr;
+    if (cudaMalloc(&sched, sizeof(int) * 2 * kCounters) != cudaSuccess) return -1.0;
+    if (cudaMemset(sched, 0, sizeof(int) * 2 * kCounters) != cudaSuccess ||
+        enqueue_many(ps.data(), io.data(), batch, parts, p->d_status, s, sched, kCounters) !=
+            cudaSuccess) {
+        cudaFree(sched);
         return -1.0;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     std::vector<double> ms;
     for (int r = 0; r < reps; ++r) {
         cudaEventRecord(e0, s);
-        enqueue_many(ps.data(), io.data(), batch, parts, p->d_status, s);
+        enqueue_many(ps.data(), io.data(), batch, parts, p->d_status, s, sched, kCounters);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float t = 0.0f;
@@ -114,6 +122,7 @@ double time_parts(const Plan *p, const std::vector<fbp_batch_io> &io, int parts,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(sched);
     std::sort(ms.begin(), ms.end());
     return ms[ms.size() / 2];
 }

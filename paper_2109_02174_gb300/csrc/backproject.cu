@@ -9,6 +9,8 @@
 // Persistent, warp-specialised kernel.  The launch owns a list of work items,
 // each one TX x TY pixel tile of one slice (one launch may hold many slices of
 // different sizes; see BpLaunch); CTA b takes items b, b + grid, b + 2 grid, ...
+// or, given a launch counter, the next untaken item whenever its ring has room
+// (which balances uneven items and CTAs that start late behind another launch)
 //   - warp NCW (the producer) walks the items' angle chunks: for each angle
 //     its lanes compute, in FP64, the first pair of the detector window the
 //     tile touches and the tile-local coordinate offset; lane 0 then issues
@@ -78,6 +80,7 @@ struct Layout {
     int prm;    // offset of params [NSTAGE][CH] float4
     int full;   // offset of full barriers [NSTAGE]
     int empty;  // offset of empty barriers [NSTAGE]
+    int item;   // offset of the work item each stage starts [NSTAGE] int (-1: no more)
     int total;  // bytes including 128 of alignment slack
     __host__ __device__ static Layout make(int wp_max, int pair_bytes, int group)
     {
@@ -87,7 +90,8 @@ struct Layout {
         L.prm = NSTAGE * L.stage;
         L.full = L.prm + NSTAGE * CH * 16;
         L.empty = L.full + NSTAGE * 8;
-        L.total = L.empty + NSTAGE * 8 + 128;
+        L.item = L.empty + NSTAGE * 8;
+        L.total = L.item + NSTAGE * 4 + 128;
         return L;
     }
 };
@@ -144,10 +148,48 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     }
     __syncthreads();
 
+    volatile int *stage_item = reinterpret_cast<volatile int *>(base_ptr + L.item);
+
     if (warp == NCW) {
         // ------------------------------------------------------------ producer
+        // The next work item comes from the launch's counter (P.sched: taken
+        // when the ring has room for the item's first stage, so a CTA that
+        // started late or drew cheap items takes more) or, without one, by
+        // striding (b, b + grid, ...).  The first stage of every item carries
+        // its index for the consumers; a stage carrying -1 ends their loop.
+        auto wait_empty = [&](uint32_t i) -> bool {
+            const uint32_t use = i / NSTAGE;
+            bool ok = true;
+            if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * (i % NSTAGE), (use - 1) & 1u);
+            return __all_sync(0xffffffffu, ok);
+        };
         uint32_t it = 0;
-        for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
+        int item = blockIdx.x;
+        for (;;) {
+            if (!wait_empty(it)) {
+                if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                return;
+            }
+            if (P.sched != nullptr) {
+                int v = 0;
+                if (lane == 0) v = atomicAdd(P.sched, 1);
+                item = __shfl_sync(0xffffffffu, v, 0);
+            }
+            if (item >= P.n_items) {
+                if (lane == 0) {
+                    const int s = (int)(it % NSTAGE);
+                    stage_item[s] = -1;
+                    mbar_arrive(full0 + 8u * s);  // no bytes: completes the phase
+                    // the last CTA past the end leaves the counter at zero for
+                    // the next launch that uses it
+                    if (P.sched != nullptr &&
+                        atomicAdd(P.sched + 1, 1) == (int)gridDim.x - 1) {
+                        atomicExch(P.sched, 0);
+                        atomicExch(P.sched + 1, 0);
+                    }
+                }
+                return;
+            }
             const int2 wi = item_of(P, item);
             const BpSlice &S = P.slices[wi.x];
             const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
@@ -156,10 +198,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             const int nch = (S.A + CH - 1) / CH;
             for (int cc = 0; cc < nch; ++cc, ++it) {
                 const int s = (int)(it % NSTAGE);
-                const uint32_t use = it / NSTAGE;
-                bool ok = true;
-                if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * s, (use - 1) & 1u);
-                if (!__all_sync(0xffffffffu, ok)) {
+                if (cc > 0 && !wait_empty(it)) {
                     if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
                     return;
                 }
@@ -178,6 +217,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     prm[s * CH + lane] = make_float4((float)cs.x, (float)cs.y,
                                                      (float)(u0 - (double)base - 0.5), 0.0f);
                 }
+                if (cc == 0 && lane == 0) stage_item[s] = item;
                 __syncwarp();
                 if (lane == 0) {
                     const uint32_t bar = full0 + 8u * s;
@@ -193,8 +233,8 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                                     &P.maps[G * wi.x + g], 2 * pb, a0 + lane, full0 + 8u * s);
                 }
             }
+            if (P.sched == nullptr) item += gridDim.x;
         }
-        return;
     }
 
     // ---------------------------------------------------------------- consumers
@@ -209,8 +249,18 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     const float2 kNegM2 = make_float2(-kMagic, -kMagic);
     const float2 kNeg1 = make_float2(-1.0f, -1.0f);
 
+    auto wait_full = [&](uint32_t i) -> bool {
+        const bool ok = mbar_wait_bounded(full0 + 8u * (i % NSTAGE), (i / NSTAGE) & 1u);
+        return __all_sync(0xffffffffu, ok);
+    };
     uint32_t it = 0;
-    for (int item = blockIdx.x; item < P.n_items; item += gridDim.x) {
+    for (;;) {
+        if (!wait_full(it)) {
+            if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+            return;
+        }
+        const int item = stage_item[it % NSTAGE];
+        if (item < 0) break;
         const int2 wi = item_of(P, item);
         const BpSlice &S = P.slices[wi.x];
         const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
@@ -226,9 +276,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
 
         for (int cc = 0; cc < nch; ++cc, ++it) {
             const int s = (int)(it % NSTAGE);
-            const uint32_t parity = (it / NSTAGE) & 1u;
-            const bool ok = mbar_wait_bounded(full0 + 8u * s, parity);
-            if (!__all_sync(0xffffffffu, ok)) {
+            if (cc > 0 && !wait_full(it)) {
                 if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
                 return;
             }

@@ -45,6 +45,11 @@ struct BpLaunch {
     int n_items;  // = tile_end[n_slices - 1]
     int wp_max;   // largest wp over the slices (sizes the shared-memory rows)
     int *status;
+    // Work distribution: NULL = CTA b takes items b, b + grid, ...; otherwise
+    // two ints {next item, CTAs done}, zero before the launch and left at zero
+    // by it, from which CTAs take items as they get room (one counter per
+    // launch in flight).
+    int *sched;
 };
 
 // Template choice: tile = (8 wx) x (32 wy) pixels, wx*wy consumer warps.

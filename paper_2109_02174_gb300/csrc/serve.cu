@@ -33,7 +33,7 @@
 
 namespace fbp {
 cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
-                         int *status, cudaStream_t s);
+                         int *status, cudaStream_t s, int *sched, int n_sched);
 }  // namespace fbp
 
 using namespace fbp;
@@ -132,6 +132,8 @@ struct Wave {
 
 using GeomKey = std::tuple<int, int, int, double, int>;
 
+constexpr int kServeCounters = 8;  // backprojection launches of one wave with a work counter
+
 }  // namespace
 
 struct fbp_server_s {
@@ -141,6 +143,7 @@ struct fbp_server_s {
     Arena arena;
     std::vector<cudaStream_t> streams;
     std::vector<bool> stream_busy;
+    int *d_sched = nullptr;  // work counters of the backprojection launches, per stream
     std::map<GeomKey, fbp_plan_t> plans;
     std::mutex mu;
     std::condition_variable cv_work;  // worker wake-up
@@ -233,8 +236,13 @@ bool launch_wave(fbp_server_s *s, Wave *w, int si)
             return false;
         q->state = ST_RUNNING;
     }
+    // the stream's work counters start each wave at zero (a wave that gave up
+    // may have left them elsewhere)
+    int *sched = s->d_sched + 2 * kServeCounters * si;
+    if (cudaMemsetAsync(sched, 0, sizeof(int) * 2 * kServeCounters, st) != cudaSuccess)
+        return false;
     if (enqueue_many(ps.data(), io.data(), n, FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT,
-                     ps[0]->d_status, st) != cudaSuccess)
+                     ps[0]->d_status, st, sched, kServeCounters) != cudaSuccess)
         return false;
     for (int i = 0; i < n; ++i) {
         Req *q = w->reqs[(size_t)i];
@@ -359,6 +367,15 @@ fbp_status fbp_server_create(fbp_server_t *out, size_t hbm_budget_bytes, int max
         delete s;
         set_error("fbp_server_create: cannot reserve %zu bytes of device memory",
                   hbm_budget_bytes);
+        return FBP_ERR_OUT_OF_MEMORY;
+    }
+    const size_t sched_bytes = sizeof(int) * 2 * kServeCounters * (size_t)n_streams;
+    if (cudaMalloc(&s->d_sched, sched_bytes) != cudaSuccess ||
+        cudaMemset(s->d_sched, 0, sched_bytes) != cudaSuccess) {
+        s->arena.release();
+        cudaFree(s->d_sched);
+        delete s;
+        set_error("fbp_server_create: cannot allocate the work counters");
         return FBP_ERR_OUT_OF_MEMORY;
     }
     for (int k = 0; k < n_streams; ++k) {
@@ -584,6 +601,7 @@ fbp_status fbp_server_destroy(fbp_server_t server)
     for (auto &kv : s->reqs) delete kv.second;
     for (auto &kv : s->plans) fbp_plan_destroy(kv.second);
     s->arena.release();
+    cudaFree(s->d_sched);
     delete s;
     return FBP_OK;
 }

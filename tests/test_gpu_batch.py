@@ -92,6 +92,41 @@ def test_batch_relaunch_sees_new_data(fbp):
         assert np.array_equal(now, _alone(fbp, plan, sino))
 
 
+def test_dynamic_work_handout_recomputes_every_tile(fbp):
+    """The batch's backprojection launches hand out work items from a counter
+    that each launch must leave at zero: after the images are cleared, every
+    relaunch (and a run through the host pipeline, whose chunks take the
+    other counter set) writes every tile again, bit-identical to alone."""
+    import torch
+    specs = small_uneven_specs(9, seed=36)
+    plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det, filter=s.filter) for s in specs]
+    sinos = [_sino(s) for s in specs]
+    want = [_alone(fbp, p, t) for p, t in zip(plans, sinos)]
+    batch = fbp.Batch(plans, sinos)
+    for _ in range(4):
+        for im in batch.images:
+            im.fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        batch.status()
+        for w, im in zip(want, batch.images):
+            assert np.array_equal(im.cpu().numpy(), w)
+    host_in = [t.cpu().contiguous().pin_memory() for t in sinos]
+    for _ in range(2):
+        host_out = [torch.full((s.n_pix, s.n_pix), float("nan")).pin_memory() for s in specs]
+        batch.run_host(host_in, host_out)
+        torch.cuda.synchronize()
+        batch.status()
+        for w, h in zip(want, host_out):
+            assert np.array_equal(h.numpy(), w)
+    for im in batch.images:
+        im.fill_(float("nan"))
+    batch.launch()
+    torch.cuda.synchronize()
+    for w, im in zip(want, batch.images):
+        assert np.array_equal(im.cpu().numpy(), w)
+
+
 def test_batch_mixes_kernel_configurations(fbp):
     """Slices whose plans pick different kernels (tile shape, FP16 pairs, Kahan)
     share one batch; each still equals its own alone result bit for bit."""
@@ -186,7 +221,8 @@ def test_batch_argument_errors(fbp):
 
 def test_run_host_pipeline_equals_device_batch(fbp):
     """fbp_batch_run_host (five pipelined chunks: sinograms in on one stream,
-    compute on the caller's, images out on a third) gives the device batch's
+    compute alternating between the caller's and a second stream, images out
+    on a fourth) gives the device batch's
     bits; a second call with new host data returns the new images, so no copy
     of one call overtakes the compute of the other.  One slice's device
     sinogram has padded rows (ld_sino > n_det), which takes the 2-D copy."""
