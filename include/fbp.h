@@ -226,9 +226,10 @@ fbp_status fbp_batch_kernel_count(fbp_batch_t batch, int *count);
  * [n_angles][n_det] float, contiguous) is copied into the batch's device
  * sinogram buffer, the slice is reconstructed, and its image is copied back to
  * host_images[i] ([n_pix][n_pix] float).  The slices are processed in up to
- * five chunks, pipelined: the sinogram copies run on one internal stream, the
- * image copies on another, the compute on `stream`, so that chunk c+1 comes in
- * and chunk c-1 goes out while chunk c computes.  One copy per slice and
+ * six chunks, pipelined: the sinogram copies run on one internal stream, the
+ * image copies on another, the compute alternately on `stream` and a third
+ * internal stream, so that chunk c+1 comes in and chunk c-1 goes out while
+ * chunk c computes, and consecutive chunks' kernels overlap.  One copy per slice and
  * direction; host buffers should be pinned for the copies to be asynchronous.
  * The work starts after what is already on `stream` and `stream` waits for the
  * last image copy, so synchronising `stream` (or an event recorded on it after

@@ -24,30 +24,31 @@ BpConfig bp_config(const Plan &p);
 using namespace fbp;
 
 // Chunks of a batch's slices that fbp_batch_run_host pipelines: while chunk c
-// computes, chunk c+1's sinograms come in and chunk c-1's images go out.  Only
-// the first chunk's copy in and the last chunk's copy out are not hidden, so
-// the chunks taper at both ends: 1/32, 7/32, 1/2, 7/32, 1/32 of the slices,
-// with boundaries on even slice counts (two slices of one plan share a
-// backprojection work item) and at least two slices at either end.  A chunk's
-// compute time does not fall in proportion to its slices (a backprojection
-// launch ends with a partly filled round of work items), so the end chunks are
-// as small as possible; a sinogram copies in four times faster than it
-// computes, so each chunk's copy still hides behind the previous compute.
-// Measured on 64 slices of 512x512, 720 angles, 725 bins: 20.5k slices/s end
-// to end with 2/14/32/14/2 slices per chunk against 20.0k with 4/12/32/12/4.
-constexpr int kRunHostChunks = 5;
+// computes, chunk c+1's sinograms come in and chunk c-1's images go out, and
+// consecutive chunks compute on alternate streams, so that a chunk's launches
+// take the SMs the previous chunk's last work items leave idle.  Only the
+// first chunk's copy in and the last chunk's copy out are not hidden, so the
+// chunks taper at both ends: 1/32, 3/32, 3/8, 3/8, 3/32, 1/32 of the slices,
+// on even slice counts (two slices of one plan share a backprojection work
+// item), at least two slices each.  Each chunk's copy in (a sinogram copies in
+// four times faster than it computes) hides behind the previous chunk's
+// compute.  Measured on 64 slices of 512x512, 720 angles, 725 bins, end to
+// end: 2/6/24/24/6/2 slices per chunk 21.3k slices/s; 2/14/32/14/2 20.8k;
+// eight chunks 2/4/10/16/16/10/4/2 21.3k; 4/12/32/12/4 on one stream with
+// static work items 20.0k.
+constexpr int kRunHostChunks = 6;
 
 // Slice index where chunk c begins (c = 0..chunks), for n slices.
 int chunk_begin(int n, int chunks, int c)
 {
     if (chunks == kRunHostChunks) {
+        static const int at[kRunHostChunks + 1] = {0, 2, 8, 32, 56, 62, 64};  // 64ths
         if (c == 0) return 0;
-        if (c == kRunHostChunks) return n;
-        const int at = c <= 2 ? c : kRunHostChunks - c;  // symmetric about the middle
-        const int t = at == 1 ? 1 : 8;                     // thirty-seconds
-        int b = 2 * ((n * t + 32) / 64);
-        if (at == 1 && b < 2) b = 2;
-        return c <= 2 ? b : n - b;
+        if (c == chunks) return n;
+        int b = 2 * ((n * at[c] + 64) / 128);  // nearest even count
+        if (b < 2 * c) b = 2 * c;
+        if (b > n - 2 * (chunks - c)) b = n - 2 * (chunks - c);
+        return b;
     }
     return (int)((long long)n * c / chunks);
 }

@@ -220,7 +220,7 @@ def test_batch_argument_errors(fbp):
 
 
 def test_run_host_pipeline_equals_device_batch(fbp):
-    """fbp_batch_run_host (five pipelined chunks: sinograms in on one stream,
+    """fbp_batch_run_host (six pipelined chunks: sinograms in on one stream,
     compute alternating between the caller's and a second stream, images out
     on a fourth) gives the device batch's
     bits; a second call with new host data returns the new images, so no copy
