@@ -85,7 +85,7 @@ typedef struct {
     int fft_len;      /* 0 = auto (next power of two >= 2*n_det-1) */
     int tile_x;       /* 0 = auto; pixel tile of one backprojection work item */
     int tile_y;       /* 0 = auto */
-    int angle_chunk;  /* 0 = auto; angles staged per shared-memory window */
+    int angle_chunk;  /* angles staged per shared-memory window: 8, 16, 32; 0 = 32 */
     double i0;        /* 0 (default): the sinogram holds line integrals p.  > 0: it
                          holds measured intensities or photon counts I of rays with
                          incident intensity i0, and every filter route converts them
