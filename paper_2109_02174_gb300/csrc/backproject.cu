@@ -80,7 +80,6 @@ struct Layout {
     int prm;    // offset of params [NSTAGE][CH] float4
     int full;   // offset of full barriers [NSTAGE]
     int empty;  // offset of empty barriers [NSTAGE]
-    int item;   // offset of the work item each stage starts [NSTAGE] int (-1: no more)
     int total;  // bytes including 128 of alignment slack
     __host__ __device__ static Layout make(int wp_max, int pair_bytes, int group)
     {
@@ -90,8 +89,7 @@ struct Layout {
         L.prm = NSTAGE * L.stage;
         L.full = L.prm + NSTAGE * CH * 16;
         L.empty = L.full + NSTAGE * 8;
-        L.item = L.empty + NSTAGE * 8;
-        L.total = L.item + NSTAGE * 4 + 128;
+        L.total = L.empty + NSTAGE * 8 + 128;
         return L;
     }
 };
@@ -148,15 +146,22 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     }
     __syncthreads();
 
-    volatile int *stage_item = reinterpret_cast<volatile int *>(base_ptr + L.item);
+    // The work item a stage belongs to rides in the otherwise unused w of the
+    // stage's first angle parameters (-1: no more work).
+    auto stage_item = [&](int s) -> volatile float & {
+        return reinterpret_cast<volatile float *>(prm + s * CH)[3];
+    };
+    // single-slice launches (MAXS = 1) always stride: no counter code in them
+    const bool dyn = MAXS > 1 && P.sched != nullptr;
 
     if (warp == NCW) {
         // ------------------------------------------------------------ producer
         // The next work item comes from the launch's counter (P.sched: taken
         // when the ring has room for the item's first stage, so a CTA that
-        // started late or drew cheap items takes more) or, without one, by
-        // striding (b, b + grid, ...).  The first stage of every item carries
-        // its index for the consumers; a stage carrying -1 ends their loop.
+        // started late or drew cheap items takes more; the first stage of
+        // every item carries its index for the consumers, and a stage
+        // carrying -1 ends their loop) or, without one, by striding (b,
+        // b + grid, ...), which the consumers follow on their own.
         auto wait_empty = [&](uint32_t i) -> bool {
             const uint32_t use = i / NSTAGE;
             bool ok = true;
@@ -166,11 +171,12 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
         uint32_t it = 0;
         int item = blockIdx.x;
         for (;;) {
+            if (!dyn && item >= P.n_items) return;  // the consumers stride too
             if (!wait_empty(it)) {
                 if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
                 return;
             }
-            if (P.sched != nullptr) {
+            if (dyn) {
                 int v = 0;
                 if (lane == 0) v = atomicAdd(P.sched, 1);
                 item = __shfl_sync(0xffffffffu, v, 0);
@@ -178,12 +184,11 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             if (item >= P.n_items) {
                 if (lane == 0) {
                     const int s = (int)(it % NSTAGE);
-                    stage_item[s] = -1;
+                    stage_item(s) = __int_as_float(-1);
                     mbar_arrive(full0 + 8u * s);  // no bytes: completes the phase
                     // the last CTA past the end leaves the counter at zero for
                     // the next launch that uses it
-                    if (P.sched != nullptr &&
-                        atomicAdd(P.sched + 1, 1) == (int)gridDim.x - 1) {
+                    if (atomicAdd(P.sched + 1, 1) == (int)gridDim.x - 1) {
                         atomicExch(P.sched, 0);
                         atomicExch(P.sched + 1, 0);
                     }
@@ -215,9 +220,9 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     pb = __double2int_rd(umin) & ~(TR::kAlign - 1);
                     const int base = pb - 1;  // bin of the window's first pair
                     prm[s * CH + lane] = make_float4((float)cs.x, (float)cs.y,
-                                                     (float)(u0 - (double)base - 0.5), 0.0f);
+                                                     (float)(u0 - (double)base - 0.5),
+                                                     __int_as_float(item));
                 }
-                if (cc == 0 && lane == 0) stage_item[s] = item;
                 __syncwarp();
                 if (lane == 0) {
                     const uint32_t bar = full0 + 8u * s;
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                                     &P.maps[G * wi.x + g], 2 * pb, a0 + lane, full0 + 8u * s);
                 }
             }
-            if (P.sched == nullptr) item += gridDim.x;
+            if (!dyn) item += gridDim.x;
         }
     }
 
@@ -254,13 +259,18 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
         return __all_sync(0xffffffffu, ok);
     };
     uint32_t it = 0;
+    int item = blockIdx.x;
     for (;;) {
-        if (!wait_full(it)) {
-            if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
-            return;
+        if (dyn) {
+            if (!wait_full(it)) {
+                if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                return;
+            }
+            item = __float_as_int(stage_item((int)(it % NSTAGE)));
+            if (item < 0) break;
+        } else if (item >= P.n_items) {
+            break;
         }
-        const int item = stage_item[it % NSTAGE];
-        if (item < 0) break;
         const int2 wi = item_of(P, item);
         const BpSlice &S = P.slices[wi.x];
         const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
 
         for (int cc = 0; cc < nch; ++cc, ++it) {
             const int s = (int)(it % NSTAGE);
-            if (cc > 0 && !wait_full(it)) {
+            if ((cc > 0 || !dyn) && !wait_full(it)) {
                 if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
                 return;
             }
@@ -344,6 +354,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 }
             }
         }
+        if (!dyn) item += gridDim.x;
     }
 }
 
