@@ -42,7 +42,8 @@ SMEM_UPDATES_PER_CLK_SM = 16
 # (profiles/bp_persistent_kernel_batch64_512x720x725.md),
 # keyed by (geometry, slices, tile_x, tile_y, angle_chunk); reported only when
 # the tuned launch is that one, null otherwise.
-BP_TRAFFIC: dict = {}
+BP_TRAFFIC = {("512x720x725", 64, 32, 32, 32): 247808768 + 53537792,
+              ("512x720x725", 64, 32, 64, 32): 250698496 + 54441472}
 ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
