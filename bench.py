@@ -391,6 +391,7 @@ def run_configs(fbp):
     out["fp64_512x720x725"] = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
                                "gupdates_per_s": gups, "fp64_peak_gupdates_per_s": fp64_peak,
                                "frac_of_fp64_peak": gups / fp64_peak,
+                               "filter": ROUTE_NAMES.get(p64.filter_path, "?") + " (FP64)",
                                "peak_basis": "nominal 1.25 TFLOP/s FP64 = 0.625 T FMA/s, "
                                              "5 FP64 ops per update"}
     spec = synthetic.cfg_large()

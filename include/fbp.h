@@ -81,7 +81,10 @@ typedef struct {
     int dtype;        /* FBP_F32 (default) or FBP_F64 (float-vs-double comparison) */
     int q_storage;    /* FBP_F32 (default) or FBP_F16: element type of the filtered sinogram */
     int accumulate;   /* FBP_ACC_PLAIN (default) or FBP_ACC_KAHAN */
-    int filter_path;  /* FBP_PATH_AUTO (default), _TOEPLITZ_TC, _FFT or _DIRECT */
+    int filter_path;  /* FBP_PATH_AUTO (default), _TOEPLITZ_TC, _FFT or _DIRECT.  AUTO
+                         takes the FFT when its length fits (8192 FP32, 4096 FP64),
+                         else the direct convolution; FP64 plans have no tensor-core
+                         route */
     int fft_len;      /* 0 = auto (next power of two >= 2*n_det-1) */
     int tile_x;       /* 0 = auto; pixel tile of one backprojection work item */
     int tile_y;       /* 0 = auto */

@@ -209,6 +209,8 @@ void free_plan(Plan *p)
     cudaFree(p->d_taps64);
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_h);
+    cudaFree(p->d_fft_tw64);
+    cudaFree(p->d_fft_h64);
     cudaFree(p->d_status);
     delete p;
 }
@@ -347,18 +349,13 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         return FBP_ERR_INVALID_ARG;
     }
     if (o.dtype == FBP_F64) {
-        // The FP64 path is the direct filter and a plain per-pixel backprojection.
+        // The FP64 path: an FFT or direct filter and a per-pixel backprojection.
         if (o.q_storage != FBP_F32 || o.accumulate != FBP_ACC_PLAIN ||
-            (o.filter_path != FBP_PATH_AUTO && o.filter_path != FBP_PATH_DIRECT)) {
+            o.filter_path == FBP_PATH_TOEPLITZ_TC) {
             set_error("fbp_plan: FP64 plans take the default q_storage/accumulate and the "
-                      "direct filter");
+                      "FFT or direct filter");
             return FBP_ERR_UNSUPPORTED;
         }
-        if (filter_direct_f64_smem_bytes(n_det) > 200 * 1024) {
-            set_error("fbp_plan: n_det %d too large for the FP64 direct filter", n_det);
-            return FBP_ERR_UNSUPPORTED;
-        }
-        o.filter_path = FBP_PATH_DIRECT;
     }
     if ((o.q_storage != FBP_F32 && o.q_storage != FBP_F16) ||
         (o.accumulate != FBP_ACC_PLAIN && o.accumulate != FBP_ACC_KAHAN)) {
@@ -385,15 +382,17 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
                   2 * n_det - 1);
         return FBP_ERR_INVALID_ARG;
     }
-    const bool fft_ok = fft_len <= kMaxFftLen && o.dtype == FBP_F32;
+    const int max_fft = o.dtype == FBP_F64 ? kMaxFftLen64 : kMaxFftLen;
+    const bool fft_ok = fft_len <= max_fft;
     int path = o.filter_path;
     if (path == FBP_PATH_AUTO) path = fft_ok ? FBP_PATH_FFT : FBP_PATH_DIRECT;
     if (path == FBP_PATH_FFT && !fft_ok) {
-        set_error("fbp_plan: FFT length %d exceeds %d", fft_len, kMaxFftLen);
+        set_error("fbp_plan: FFT length %d exceeds %d", fft_len, max_fft);
         return FBP_ERR_UNSUPPORTED;
     }
-    if (path == FBP_PATH_DIRECT && o.dtype == FBP_F32 &&
-        filter_direct_smem_bytes(n_det) > 200 * 1024) {
+    if (path == FBP_PATH_DIRECT &&
+        (o.dtype == FBP_F64 ? filter_direct_f64_smem_bytes(n_det)
+                            : filter_direct_smem_bytes(n_det)) > 200 * 1024) {
         set_error("fbp_plan: n_det %d too large for the direct filter", n_det);
         return FBP_ERR_UNSUPPORTED;
     }
@@ -488,31 +487,51 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess && p->filter_path == FBP_PATH_FFT) {
         const int N = p->fft_len;
-        // twiddles and spectrum stored twice over (one copy per transform of a
-        // packed pair): tw[t] = (c, c, s, s), h[f] = (H, H)
-        std::vector<float4> tw((size_t)N);
-        std::vector<double> ct((size_t)N);
+        std::vector<double> ct((size_t)N), st((size_t)N);
         for (int t = 0; t < N; ++t) {
             const double a = 2.0 * M_PI * (double)t / (double)N;
             ct[(size_t)t] = std::cos(a);
-            const float c = (float)std::cos(a), sn = (float)-std::sin(a);
-            tw[(size_t)t] = make_float4(c, c, sn, sn);
+            st[(size_t)t] = std::sin(a);
         }
         // H[f] = sum_m tau h(m) e^{-2 pi i f m / N} = tau h(0) + 2 sum_{m>0} tau h(m) cos(2 pi f m / N)
-        std::vector<float2> hs((size_t)N);
+        std::vector<double> hs((size_t)N);
         for (int f = 0; f < N; ++f) {
             double acc = taps[(size_t)(n_det - 1)];
             for (int m = 1; m < n_det; ++m)
                 acc += 2.0 * taps[(size_t)(n_det - 1 + m)] * ct[(size_t)(((long)f * m) % N)];
-            const float hv = (float)(acc / (double)N);
-            hs[(size_t)f] = make_float2(hv, hv);
+            hs[(size_t)f] = acc / (double)N;
         }
-        e = cudaMalloc(&p->d_fft_tw, sizeof(float4) * (size_t)N);
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_fft_h, sizeof(float2) * (size_t)N);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_fft_tw, tw.data(), sizeof(float4) * (size_t)N, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_fft_h, hs.data(), sizeof(float2) * (size_t)N, cudaMemcpyHostToDevice);
+        if (p->dtype == FBP_F64) {
+            std::vector<double2> tw((size_t)N);
+            for (int t = 0; t < N; ++t) tw[(size_t)t] = make_double2(ct[(size_t)t], -st[(size_t)t]);
+            e = cudaMalloc(&p->d_fft_tw64, sizeof(double2) * (size_t)N);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_fft_h64, sizeof(double) * (size_t)N);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->d_fft_tw64, tw.data(), sizeof(double2) * (size_t)N,
+                               cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->d_fft_h64, hs.data(), sizeof(double) * (size_t)N,
+                               cudaMemcpyHostToDevice);
+        } else {
+            // twiddles and spectrum stored twice over (one copy per transform of a
+            // packed pair): tw[t] = (c, c, s, s), h[f] = (H, H)
+            std::vector<float4> tw((size_t)N);
+            std::vector<float2> h2((size_t)N);
+            for (int t = 0; t < N; ++t) {
+                const float c = (float)ct[(size_t)t], sn = (float)-st[(size_t)t];
+                tw[(size_t)t] = make_float4(c, c, sn, sn);
+                const float hv = (float)hs[(size_t)t];
+                h2[(size_t)t] = make_float2(hv, hv);
+            }
+            e = cudaMalloc(&p->d_fft_tw, sizeof(float4) * (size_t)N);
+            if (e == cudaSuccess) e = cudaMalloc(&p->d_fft_h, sizeof(float2) * (size_t)N);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->d_fft_tw, tw.data(), sizeof(float4) * (size_t)N,
+                               cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->d_fft_h, h2.data(), sizeof(float2) * (size_t)N,
+                               cudaMemcpyHostToDevice);
+        }
     }
     if (e == cudaSuccess && p->filter_path == FBP_PATH_TOEPLITZ_TC) {
         p->tc = new TcTables();
@@ -573,7 +592,10 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
         return FBP_ERR_INVALID_ARG;
     }
     cudaError_t e;
-    if (p->dtype == FBP_F64)
+    if (p->dtype == FBP_F64 && p->filter_path == FBP_PATH_FFT)
+        e = launch_filter_fft_f64(*p, static_cast<const double *>(sino), ld_sino,
+                                  static_cast<double *>(filtered), stream);
+    else if (p->dtype == FBP_F64)
         e = launch_filter_direct_f64(*p, static_cast<const double *>(sino), ld_sino,
                                      static_cast<double *>(filtered), stream);
     else if (p->filter_path == FBP_PATH_FFT)

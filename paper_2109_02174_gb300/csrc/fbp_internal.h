@@ -11,7 +11,8 @@
 
 namespace fbp {
 
-constexpr int kMaxFftLen = 8192;  // FP32 FFT route: two N-point complex buffers in shared memory
+constexpr int kMaxFftLen = 8192;    // FP32 FFT route: two N-point complex buffers in shared memory
+constexpr int kMaxFftLen64 = 4096;  // FP64 FFT route: two N-point double2 buffers (128 KB)
 constexpr int kFftMaxSlices = 64; // slices per batched FFT launch
 
 struct TcTables;  // tensor-core filter tables (filter_tc.cuh)
@@ -46,6 +47,8 @@ struct Plan {
     double *d_taps64;   // same in FP64
     float4 *d_fft_tw;   // FFT route: (c, c, s, s) with c + i s = exp(-2 pi i t / N), t < N
     float2 *d_fft_h;    // FFT route: (H, H), H = DFT_N of the circular taps / N (real, even)
+    double2 *d_fft_tw64;  // FP64 FFT route: exp(-2 pi i t / N), t < N
+    double *d_fft_h64;    // FP64 FFT route: H = DFT_N of the circular taps / N
     const float *d_row_weight;  // FFT route, optional: [row_weight_rows][D] factors applied to
     int row_weight_rows;        //   row r's values on load (row r uses table row r mod rows)
     int *d_status;      // device status word (0 = ok)
@@ -88,8 +91,11 @@ cudaError_t backproject_slice(const Plan &p, const void *q, float *image, cudaSt
 // FP64 path (fp64.cu).
 cudaError_t launch_filter_direct_f64(const Plan &p, const double *sino, int ld, double *q,
                                      cudaStream_t s);
+cudaError_t launch_filter_fft_f64(const Plan &p, const double *sino, int ld, double *q,
+                                  cudaStream_t s);
 cudaError_t launch_backproject_f64(const Plan &p, const double *q, double *image, cudaStream_t s);
 size_t filter_direct_f64_smem_bytes(int D);
+size_t filter_fft_f64_smem_bytes(int N);
 
 cudaError_t launch_radon_forward_f32(const Plan &p, const float *image, float *sino,
                                      cudaStream_t s);

@@ -1,10 +1,13 @@
 // FP64 variant of the whole path, for the paper's float-vs-double comparison
 // (section "Results and discussion", double data type).  Same operator as the
-// FP32 path: the direct ramp-filter convolution (the text after Eq. 2) written
-// as (mid, slope) pairs of doubles, then Eq. 2 per pixel with linear
+// FP32 path: the ramp-filter convolution (the text after Eq. 2) written as
+// (mid, slope) pairs of doubles, then Eq. 2 per pixel with linear
 // interpolation, angles summed in order.  Plain CUDA-core code: GB300's FP64
-// rate is a small fraction of its FP32 rate, so this path is for accuracy, not
-// throughput.
+// rate is a small fraction of its FP32 rate, so the kernels count FP64
+// operations: the filter goes through an FP64 FFT (about 80 operations per
+// bin instead of the direct convolution's 2 D), and the backprojection spends
+// about six per update (position by one addition per pixel, rounding by the
+// 1.5 * 2^52 shift, fraction, lerp, sum).
 #include "fbp_internal.h"
 #include "lambert.cuh"
 
@@ -45,30 +48,159 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// One thread per pixel; pairs are read through the cache (each row of pairs is
-// reused by every pixel of the image).
+// FFT route: one CTA per pair of rows, the two rows as the real and imaginary
+// parts of one N-point complex sequence (N a power of two >= 2D-1, so the
+// circular convolution is the linear one on [0, D)), transformed in shared
+// memory by a radix-4 Stockham FFT (one radix-2 pass first when log2 N is odd),
+// multiplied by the real, even spectrum of the circular taps (divided by N)
+// and transformed back: the real part is row a's filtered row, the imaginary
+// part row b's.
+constexpr int kFft64Threads = 256;
+
+__device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 dsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 dmul(double2 a, double2 w)
+{
+    return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+
+// Stockham passes x -> y -> x ... over N = 2^L points (natural order in and
+// out); tw[t] = exp(-2 pi i t / N), conjugated for the inverse.  Returns the
+// buffer that holds the result.
+template <bool INV>
+__device__ double2 *fft64(double2 *x, double2 *y, const double2 *__restrict__ tw, int N, int L)
+{
+    int Ns = 1;
+    if (L & 1) {  // radix-2 pass with Ns = 1: no twiddles
+        for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
+            const double2 v0 = x[j], v1 = x[j + N / 2];
+            y[2 * j] = dadd(v0, v1);
+            y[2 * j + 1] = dsub(v0, v1);
+        }
+        __syncthreads();
+        double2 *t = x; x = y; y = t;
+        Ns = 2;
+    }
+    for (; Ns < N; Ns <<= 2) {
+        const int st = N / (4 * Ns);
+        for (int j = threadIdx.x; j < N / 4; j += blockDim.x) {
+            const int k = j & (Ns - 1);
+            double2 w1 = __ldg(&tw[k * st]), w2 = __ldg(&tw[2 * k * st]), w3 = __ldg(&tw[3 * k * st]);
+            if (INV) {
+                w1.y = -w1.y;
+                w2.y = -w2.y;
+                w3.y = -w3.y;
+            }
+            const double2 v0 = x[j];
+            const double2 v1 = dmul(x[j + N / 4], w1);
+            const double2 v2 = dmul(x[j + N / 2], w2);
+            const double2 v3 = dmul(x[j + 3 * (N / 4)], w3);
+            const double2 a0 = dadd(v0, v2), a1 = dsub(v0, v2), a2 = dadd(v1, v3);
+            const double2 d = dsub(v1, v3);
+            const double2 a3 = INV ? make_double2(-d.y, d.x) : make_double2(d.y, -d.x);  // +-i d
+            const int idx = ((j - k) << 2) + k;
+            y[idx] = dadd(a0, a2);
+            y[idx + Ns] = dadd(a1, a3);
+            y[idx + 2 * Ns] = dsub(a0, a2);
+            y[idx + 3 * Ns] = dsub(a1, a3);
+        }
+        __syncthreads();
+        double2 *t = x; x = y; y = t;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(kFft64Threads)
+    filter_fft_f64_kernel(const double *__restrict__ sino, int ld,
+                          const double2 *__restrict__ tw, const double *__restrict__ hs,
+                          double *__restrict__ q, int A, int D, int N, int L, int pitch,
+                          double i0)
+{
+    extern __shared__ double2 sz[];
+    double2 *x = sz, *y = sz + N;
+    const int ra = 2 * blockIdx.x, rb = ra + 1;
+    const bool has_b = rb < A;
+    const double *pa = sino + (size_t)ra * ld;
+    const double *pb = sino + (size_t)(has_b ? rb : ra) * ld;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        if (j < D) {
+            a = line_integral(pa[j], i0);
+            if (has_b) b = line_integral(pb[j], i0);
+        }
+        x[j] = make_double2(a, b);
+    }
+    __syncthreads();
+    double2 *z = fft64<false>(x, y, tw, N, L);
+    double2 *o = (z == x) ? y : x;
+    for (int f = threadIdx.x; f < N; f += blockDim.x) {
+        const double h = __ldg(&hs[f]);
+        z[f] = make_double2(z[f].x * h, z[f].y * h);
+    }
+    __syncthreads();
+    z = fft64<true>(z, o, tw, N, L);
+    // z[k] = (Q_a[k], Q_b[k]); pair p = ((Q[p-1] + Q[p]) / 2, Q[p] - Q[p-1]),
+    // Q zero outside [0, D); pairs past D are zero
+    double2 *qa = reinterpret_cast<double2 *>(q + (size_t)ra * pitch);
+    double2 *qb = reinterpret_cast<double2 *>(q + (size_t)rb * pitch);
+    for (int p = threadIdx.x; p < pitch / 2; p += blockDim.x) {
+        double2 ma = make_double2(0.0, 0.0), mb = ma;
+        if (p <= D) {
+            const double2 lo = p > 0 ? z[p - 1] : make_double2(0.0, 0.0);
+            const double2 hi = p < D ? z[p] : make_double2(0.0, 0.0);
+            ma = make_double2((lo.x + hi.x) * 0.5, hi.x - lo.x);
+            mb = make_double2((lo.y + hi.y) * 0.5, hi.y - lo.y);
+        }
+        qa[p] = ma;
+        if (has_b) qb[p] = mb;
+    }
+}
+
+// Backprojection: one thread per 4 pixels of a column (rows r0 + 16 j), the
+// pairs read through the cache (every row of pairs serves the whole image).
+// Per update: the local coordinate v = u - 1/2 (the next pixel's by one
+// addition), the shift by 1.5 * 2^52 that leaves round(v) = floor(u) in the
+// low word, the fraction w = v - round(v), then mid + w * slope.
+constexpr int kBp64Rows = 4;
+
 __global__ void __launch_bounds__(256)
     backproject_f64_kernel(const double *__restrict__ q, int pitch,
                            const double2 *__restrict__ trig, double *__restrict__ image, int n,
                            int A, int D, double half_n, double half_d, double scale)
 {
+    constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
     const int c = blockIdx.x * 16 + (threadIdx.x & 15);
-    const int r = blockIdx.y * 16 + (threadIdx.x >> 4);
-    if (r >= n || c >= n) return;
+    const int r0 = blockIdx.y * (16 * kBp64Rows) + (threadIdx.x >> 4);
     const double x = (double)c - half_n;
-    const double y = (double)r - half_n;
-    double acc = 0.0;
+    const double y0 = (double)r0 - half_n;
+    const double off = half_d - 0.5;
+    double acc[kBp64Rows];
+#pragma unroll
+    for (int j = 0; j < kBp64Rows; ++j) acc[j] = 0.0;
     for (int i = 0; i < A; ++i) {
         const double2 cs = __ldg(&trig[i]);
-        const double u = x * cs.x + y * cs.y + half_d;
-        const double fk = floor(u);
-        const int p = (int)fk + 1;  // pair of bin floor(u)
-        if (p >= 0 && p <= D) {
-            const double2 ms = __ldg(reinterpret_cast<const double2 *>(q + (size_t)i * pitch) + p);
-            acc += fma(u - fk - 0.5, ms.y, ms.x);
+        const double2 *row = reinterpret_cast<const double2 *>(q + (size_t)i * pitch);
+        const double dv = 16.0 * cs.y;
+        double v = fma(x, cs.x, fma(y0, cs.y, off));
+#pragma unroll
+        for (int j = 0; j < kBp64Rows; ++j) {
+            if (j > 0) v += dv;
+            const double t = v + kShift;
+            const int p = __double2loint(t) + 1;  // pair of bin floor(u)
+            const double w = v - (t - kShift);
+            if ((unsigned)p <= (unsigned)D) {
+                const double2 ms = __ldg(&row[p]);
+                acc[j] += fma(w, ms.y, ms.x);
+            }
         }
     }
-    image[(size_t)r * n + c] = acc * scale;
+    if (c < n) {
+#pragma unroll
+        for (int j = 0; j < kBp64Rows; ++j) {
+            const int r = r0 + 16 * j;
+            if (r < n) image[(size_t)r * n + c] = acc[j] * scale;
+        }
+    }
 }
 
 }  // namespace
@@ -87,9 +219,26 @@ cudaError_t launch_filter_direct_f64(const Plan &p, const double *sino, int ld, 
     return cudaGetLastError();
 }
 
+size_t filter_fft_f64_smem_bytes(int N) { return 2 * sizeof(double2) * (size_t)N; }
+
+cudaError_t launch_filter_fft_f64(const Plan &p, const double *sino, int ld, double *q,
+                                  cudaStream_t s)
+{
+    const int N = p.fft_len;
+    int L = 0;
+    while ((1 << L) < N) ++L;
+    const size_t smem = filter_fft_f64_smem_bytes(N);
+    cudaError_t e = cudaFuncSetAttribute(filter_fft_f64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    filter_fft_f64_kernel<<<(p.A + 1) / 2, kFft64Threads, smem, s>>>(
+        sino, ld, p.d_fft_tw64, p.d_fft_h64, q, p.A, p.D, N, L, p.pitch, p.i0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backproject_f64(const Plan &p, const double *q, double *image, cudaStream_t s)
 {
-    dim3 grid((p.n + 15) / 16, (p.n + 15) / 16);
+    dim3 grid((p.n + 15) / 16, (p.n + 16 * kBp64Rows - 1) / (16 * kBp64Rows));
     backproject_f64_kernel<<<grid, 256, 0, s>>>(q, p.pitch, p.d_trig64, image, p.n, p.A, p.D,
                                                 0.5 * (double)(p.n - 1), 0.5 * (double)(p.D - 1),
                                                 p.scale64);

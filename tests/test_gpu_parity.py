@@ -286,11 +286,12 @@ def test_fp16_pairs_error_is_stated(fbp):
 FP64_REL = 1e-10
 
 
-def _fp64_slice(fbp, spec):
+def _fp64_slice(fbp, spec, filter_path=0):
     import torch
     th = synthetic.default_angles(spec.n_angles)
     sino = synthetic.sinogram(spec, th)
-    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter, dtype=1)
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter, dtype=1,
+                    filter_path=filter_path)
     assert plan.dtype == torch.float64
     got = plan.reconstruct(torch.from_numpy(sino).cuda())
     torch.cuda.synchronize()
@@ -299,23 +300,50 @@ def _fp64_slice(fbp, spec):
     return errors(got.cpu().numpy(), ref)
 
 
-def test_fp64_float_double_slice_512(fbp):
-    """The float-vs-double configuration on the FP64 GPU path: <= 1e-10 of max|f|."""
-    e_max, e_rms = _fp64_slice(fbp, synthetic.cfg_float_double())
-    print(f"fp64: max {e_max:.3e} rmse {e_rms:.3e}")
+FP64_PATHS = {"fft": 2, "direct": 3}
+
+
+@pytest.mark.parametrize("path", sorted(FP64_PATHS))
+def test_fp64_float_double_slice_512(fbp, path):
+    """The float-vs-double configuration on the FP64 GPU path, FFT and direct
+    filter: <= 1e-10 of max|f|."""
+    e_max, e_rms = _fp64_slice(fbp, synthetic.cfg_float_double(), FP64_PATHS[path])
+    print(f"fp64 {path}: max {e_max:.3e} rmse {e_rms:.3e}")
     assert e_max <= FP64_REL
 
 
-@pytest.mark.parametrize("n,A,D", [(3, 2, 5), (33, 17, 40), (70, 21, 60)])
-def test_fp64_small_and_ragged(fbp, n, A, D):
+@pytest.mark.parametrize("path", sorted(FP64_PATHS))
+@pytest.mark.parametrize("n,A,D", [(3, 2, 5), (33, 17, 40), (70, 21, 60), (65, 33, 93)])
+def test_fp64_small_and_ragged(fbp, n, A, D, path):
+    """Odd angle counts leave the last row of the FFT route's row pairs alone;
+    FFT lengths 16, 128 (one radix-2 pass first) and 256."""
     spec = synthetic.SliceSpec(n, A, D, 4, seed=n + A, filter=0)
-    e_max, _ = _fp64_slice(fbp, spec)
+    e_max, _ = _fp64_slice(fbp, spec, FP64_PATHS[path])
     assert e_max <= FP64_REL
+
+
+def test_fp64_fft_route_is_the_default_and_matches_direct(fbp):
+    """AUTO resolves to the FP64 FFT when its length fits; the two FP64 routes
+    give the same filtered pairs to rounding (linear convolution either way)."""
+    import torch
+    spec = synthetic.SliceSpec(150, 91, synthetic.det_for(150), 6, seed=77, filter=1)
+    th = synthetic.default_angles(spec.n_angles)
+    sino = torch.from_numpy(synthetic.sinogram(spec, th)).cuda()
+    auto = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=1, dtype=1)
+    direct = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=1, dtype=1, filter_path=3)
+    assert auto.filter_path == 2 and auto.fft_len == 512
+    qa, qd = auto.filter(sino), direct.filter(sino)
+    torch.cuda.synchronize()
+    qa, qd = qa.cpu().numpy(), qd.cpu().numpy()
+    assert np.abs(qa - qd).max() <= 1e-12 * np.abs(qd).max()
 
 
 def test_fp64_rejects_fp32_only_options(fbp):
     with pytest.raises(fbp.FbpError) as e:
-        fbp.Plan(64, 10, 91, dtype=1, filter_path=2)
+        fbp.Plan(64, 10, 91, dtype=1, filter_path=1)
+    assert e.value.status == fbp.FBP_ERR_UNSUPPORTED
+    with pytest.raises(fbp.FbpError) as e:
+        fbp.Plan(64, 10, 91, dtype=1, filter_path=2, fft_len=8192)
     assert e.value.status == fbp.FBP_ERR_UNSUPPORTED
     with pytest.raises(fbp.FbpError) as e:
         fbp.Plan(64, 10, 91, dtype=1, q_storage=2)
