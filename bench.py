@@ -654,6 +654,10 @@ def run_ours(args, rank, world, local_rank):
                                 "kind": "oracle",
                                 "sample": "one full slice of the workload (FP64 C oracle, "
                                           "filter + backprojection, all host cores)"}
+        # the paper's sequential CPU arm: the same slice on one host core
+        t1 = cpu_fbp_time([spec0], sample, 1)
+        line["cpu_one_core"] = {"value": 1.0 / t1, "unit": "slices/s", "cores": 1,
+                                "kind": "oracle", "sample": "the same slice on one host core"}
     for b in (full, bp_only, filt_only):
         b.close()
     if world == 1 and args.serve_seconds > 0:

@@ -313,10 +313,12 @@ def test_fp64_float_double_slice_512(fbp, path):
 
 
 @pytest.mark.parametrize("path", sorted(FP64_PATHS))
-@pytest.mark.parametrize("n,A,D", [(3, 2, 5), (33, 17, 40), (70, 21, 60), (65, 33, 93)])
+@pytest.mark.parametrize("n,A,D", [(3, 2, 5), (33, 17, 40), (70, 21, 60), (65, 33, 93),
+                                   (64, 9, 1500)])
 def test_fp64_small_and_ragged(fbp, n, A, D, path):
     """Odd angle counts leave the last row of the FFT route's row pairs alone;
-    FFT lengths 16, 128 (one radix-2 pass first) and 256."""
+    FFT lengths 16, 128 (one radix-2 pass first), 256 and 4096 (the longest
+    FP64 FFT, 128 KB of shared memory)."""
     spec = synthetic.SliceSpec(n, A, D, 4, seed=n + A, filter=0)
     e_max, _ = _fp64_slice(fbp, spec, FP64_PATHS[path])
     assert e_max <= FP64_REL
