@@ -156,21 +156,25 @@ __global__ void __launch_bounds__(kFft64Threads)
     }
 }
 
-// Backprojection: one thread per 4 pixels of a column (rows r0 + 16 j), the
-// pairs read through the cache (every row of pairs serves the whole image).
+// Backprojection: 16 x 16 pixels per 64-thread block, one thread per 4 pixels
+// of a column (rows r0 + 4 j), the pairs read through the cache (every row of
+// pairs serves the whole image).  Small blocks keep the FP64 work even across
+// the SMs (a 512^2 image is 1024 blocks: with 256 blocks of 16 x 64 pixels,
+// two thirds of the SMs held two and the rest one).
 // Per update: the local coordinate v = u - 1/2 (the next pixel's by one
 // addition), the shift by 1.5 * 2^52 that leaves round(v) = floor(u) in the
 // low word, the fraction w = v - round(v), then mid + w * slope.
 constexpr int kBp64Rows = 4;
+constexpr int kBp64Threads = 16 * 16 / kBp64Rows;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kBp64Threads)
     backproject_f64_kernel(const double *__restrict__ q, int pitch,
                            const double2 *__restrict__ trig, double *__restrict__ image, int n,
                            int A, int D, double half_n, double half_d, double scale)
 {
     constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
     const int c = blockIdx.x * 16 + (threadIdx.x & 15);
-    const int r0 = blockIdx.y * (16 * kBp64Rows) + (threadIdx.x >> 4);
+    const int r0 = blockIdx.y * 16 + (threadIdx.x >> 4);
     const double x = (double)c - half_n;
     const double y0 = (double)r0 - half_n;
     const double off = half_d - 0.5;
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(256)
     for (int i = 0; i < A; ++i) {
         const double2 cs = __ldg(&trig[i]);
         const double2 *row = reinterpret_cast<const double2 *>(q + (size_t)i * pitch);
-        const double dv = 16.0 * cs.y;
+        const double dv = (double)(16 / kBp64Rows) * cs.y;
         double v = fma(x, cs.x, fma(y0, cs.y, off));
 #pragma unroll
         for (int j = 0; j < kBp64Rows; ++j) {
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(256)
     if (c < n) {
 #pragma unroll
         for (int j = 0; j < kBp64Rows; ++j) {
-            const int r = r0 + 16 * j;
+            const int r = r0 + (16 / kBp64Rows) * j;
             if (r < n) image[(size_t)r * n + c] = acc[j] * scale;
         }
     }
@@ -238,8 +242,8 @@ cudaError_t launch_filter_fft_f64(const Plan &p, const double *sino, int ld, dou
 
 cudaError_t launch_backproject_f64(const Plan &p, const double *q, double *image, cudaStream_t s)
 {
-    dim3 grid((p.n + 15) / 16, (p.n + 16 * kBp64Rows - 1) / (16 * kBp64Rows));
-    backproject_f64_kernel<<<grid, 256, 0, s>>>(q, p.pitch, p.d_trig64, image, p.n, p.A, p.D,
+    dim3 grid((p.n + 15) / 16, (p.n + 15) / 16);
+    backproject_f64_kernel<<<grid, kBp64Threads, 0, s>>>(q, p.pitch, p.d_trig64, image, p.n, p.A, p.D,
                                                 0.5 * (double)(p.n - 1), 0.5 * (double)(p.D - 1),
                                                 p.scale64);
     return cudaGetLastError();
