@@ -132,10 +132,14 @@ fbp_status fbp_plan_query(fbp_plan_t plan, int *q_pitch, int *fft_len, int *filt
  * form for fbp_backproject.
  *   sino      device [n_angles][ld_sino] float, ld_sino >= n_det
  *   filtered  device [n_angles][q_pitch] of the q_storage type (float, or half for
- *             FBP_F16).  Row i holds, for every bin k = -1 .. n_det-1, the pair
- *               mid_k = (Q_i[k] + Q_i[k+1]) / 2,   slope_k = Q_i[k+1] - Q_i[k]
- *             at elements 2(k+1) and 2(k+1)+1, with Q_i zero outside [0, n_det)
- *             (so the linear interpolant on [k, k+1] is mid_k + (u - k - 1/2) slope_k);
+ *             FBP_F16; double for FBP_F64 plans).  Row i holds, for every bin
+ *             k = -1 .. n_det-1, a pair at elements 2(k+1) and 2(k+1)+1, with Q_i
+ *             zero outside [0, n_det):
+ *               FP32/FP16 plans: mid_k = (Q_i[k] + Q_i[k+1]) / 2,
+ *                 slope_k = Q_i[k+1] - Q_i[k]  (the interpolant on [k, k+1] is
+ *                 mid_k + (u - k - 1/2) slope_k);
+ *               FP64 plans: a_k = 2 Q_i[k] - Q_i[k+1], d_k = Q_i[k+1] - Q_i[k]
+ *                 (the interpolant is a_k + (1 + u - k) d_k);
  *             elements 2(n_det+1) .. q_pitch-1 are written as zero.
  */
 fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filtered,

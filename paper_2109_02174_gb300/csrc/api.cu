@@ -1,4 +1,5 @@
 // C ABI of libfbp (include/fbp.h): argument checks, plan tables, dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -210,6 +211,7 @@ void free_plan(Plan *p)
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_h);
     cudaFree(p->d_fft_tw64);
+    cudaFree(p->d_trig_fx);
     cudaFree(p->d_fft_h64);
     cudaFree(p->d_status);
     delete p;
@@ -482,6 +484,36 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_taps32, taps32.data(), sizeof(float) * taps32.size(),
                        cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->dtype == FBP_F64) {
+        // Fixed-point detector coordinate of the FP64 backprojection: S fraction
+        // bits, as many as keep |u| 2^S (with a margin of a partial block of
+        // pixels beyond the image) below 2^62, at most 48.
+        double cmax = 0.0, smax = 0.0;
+        for (const double2 &t : trig) {
+            cmax = std::max(cmax, std::fabs(t.x));
+            smax = std::max(smax, std::fabs(t.y));
+        }
+        const double half = 0.5 * (double)(n_pix - 1) + 16.0;
+        const double bound = half * (cmax + smax) + 0.5 * (double)(n_det - 1) + 1.0;
+        int b = 0;
+        while (std::ldexp(1.0, b) <= bound) ++b;
+        p->fx_shift = std::min(48, 62 - b);
+        if (p->fx_shift < 24) {
+            free_plan(p);
+            set_error("fbp_plan: detector coordinates up to %.3g bins are beyond the FP64 "
+                      "path's fixed-point range", bound);
+            return FBP_ERR_UNSUPPORTED;
+        }
+        const double unit = std::ldexp(1.0, p->fx_shift - 1);
+        std::vector<longlong2> fx(trig.size());
+        for (size_t i = 0; i < trig.size(); ++i)
+            fx[i] = make_longlong2(std::llround(trig[i].x * unit), std::llround(trig[i].y * unit));
+        p->half_d_fx = std::llround(0.5 * (double)(n_det - 1) * std::ldexp(1.0, p->fx_shift));
+        e = cudaMalloc(&p->d_trig_fx, sizeof(longlong2) * fx.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_trig_fx, fx.data(), sizeof(longlong2) * fx.size(),
+                           cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_taps64, taps.data(), sizeof(double) * taps.size(),
                        cudaMemcpyHostToDevice);

@@ -47,6 +47,9 @@ struct Plan {
     double *d_taps64;   // same in FP64
     float4 *d_fft_tw;   // FFT route: (c, c, s, s) with c + i s = exp(-2 pi i t / N), t < N
     float2 *d_fft_h;    // FFT route: (H, H), H = DFT_N of the circular taps / N (real, even)
+    longlong2 *d_trig_fx;  // FP64 path: (cos, sin) / tau in units of 2^-(fx_shift-1)
+    long long half_d_fx;   // FP64 path: (n_det - 1) / 2 in units of 2^-fx_shift
+    int fx_shift;          // FP64 path: fraction bits of the fixed-point detector coordinate
     double2 *d_fft_tw64;  // FP64 FFT route: exp(-2 pi i t / N), t < N
     double *d_fft_h64;    // FP64 FFT route: H = DFT_N of the circular taps / N
     const float *d_row_weight;  // FFT route, optional: [row_weight_rows][D] factors applied to

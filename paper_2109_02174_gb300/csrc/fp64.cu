@@ -5,9 +5,11 @@
 // interpolation, angles summed in order.  Plain CUDA-core code: GB300's FP64
 // rate is a small fraction of its FP32 rate, so the kernels count FP64
 // operations: the filter goes through an FP64 FFT (about 80 operations per
-// bin instead of the direct convolution's 2 D), and the backprojection spends
-// about six per update (position by one addition per pixel, rounding by the
-// 1.5 * 2^52 shift, fraction, lerp, sum).
+// bin instead of the direct convolution's 2 D), and the backprojection keeps
+// the detector coordinate in 64-bit fixed point on the integer pipes and
+// spends two FP64 operations per update (lerp, sum).  FP64 pairs are
+// (a_k, d_k) = (2 Q[k] - Q[k+1], Q[k+1] - Q[k]) for bins k = -1 .. D-1, so
+// the interpolant on [k, k+1] at fraction f is the single FMA a_k + (1 + f) d_k.
 #include "fbp_internal.h"
 #include "lambert.cuh"
 
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(256)
     double2 *row = reinterpret_cast<double2 *>(q + (size_t)i * pitch);
     for (int p = threadIdx.x; p < pitch / 2; p += blockDim.x) {
         if (p <= D)
-            row[p] = make_double2((sq[p] + sq[p + 1]) * 0.5, sq[p + 1] - sq[p]);
+            row[p] = make_double2(2.0 * sq[p] - sq[p + 1], sq[p + 1] - sq[p]);
         else
             row[p] = make_double2(0.0, 0.0);
     }
@@ -139,8 +141,8 @@ __global__ void __launch_bounds__(kFft64Threads)
     }
     __syncthreads();
     z = fft64<true>(z, o, tw, N, L);
-    // z[k] = (Q_a[k], Q_b[k]); pair p = ((Q[p-1] + Q[p]) / 2, Q[p] - Q[p-1]),
-    // Q zero outside [0, D); pairs past D are zero
+    // z[k] = (Q_a[k], Q_b[k]); pair p = (2 Q[p-1] - Q[p], Q[p] - Q[p-1]), Q
+    // zero outside [0, D); pairs past D are zero
     double2 *qa = reinterpret_cast<double2 *>(q + (size_t)ra * pitch);
     double2 *qb = reinterpret_cast<double2 *>(q + (size_t)rb * pitch);
     for (int p = threadIdx.x; p < pitch / 2; p += blockDim.x) {
@@ -148,8 +150,8 @@ __global__ void __launch_bounds__(kFft64Threads)
         if (p <= D) {
             const double2 lo = p > 0 ? z[p - 1] : make_double2(0.0, 0.0);
             const double2 hi = p < D ? z[p] : make_double2(0.0, 0.0);
-            ma = make_double2((lo.x + hi.x) * 0.5, hi.x - lo.x);
-            mb = make_double2((lo.y + hi.y) * 0.5, hi.y - lo.y);
+            ma = make_double2(2.0 * lo.x - hi.x, hi.x - lo.x);
+            mb = make_double2(2.0 * lo.y - hi.y, hi.y - lo.y);
         }
         qa[p] = ma;
         if (has_b) qb[p] = mb;
@@ -159,42 +161,45 @@ __global__ void __launch_bounds__(kFft64Threads)
 // Backprojection: 16 x 16 pixels per 64-thread block, one thread per 4 pixels
 // of a column (rows r0 + 4 j), the pairs read through the cache (every row of
 // pairs serves the whole image).  Small blocks keep the FP64 work even across
-// the SMs (a 512^2 image is 1024 blocks: with 256 blocks of 16 x 64 pixels,
-// two thirds of the SMs held two and the rest one).
-// Per update: the local coordinate v = u - 1/2 (the next pixel's by one
-// addition), the shift by 1.5 * 2^52 that leaves round(v) = floor(u) in the
-// low word, the fraction w = v - round(v), then mid + w * slope.
+// the SMs (a 512^2 image is 1024 blocks).  The detector coordinate
+//     u = (X2 cos + Y2 sin) / (2 tau) + (D - 1) / 2,  X2 = 2c - (n-1), Y2 = 2r - (n-1)
+// is a 64-bit integer in units of 2^-S (cos/tau and sin/tau in units of
+// 2^-(S-1) from a plan table), so the next pixel's coordinate is an integer
+// addition, floor(u) a shift, and 1 + (u - floor(u)) a double assembled from
+// the fraction's bits: the FP64 pipe, about two operations per clock per SM
+// on GB300, does only the interpolating FMA and the sum.
 constexpr int kBp64Rows = 4;
 constexpr int kBp64Threads = 16 * 16 / kBp64Rows;
 
 __global__ void __launch_bounds__(kBp64Threads)
     backproject_f64_kernel(const double *__restrict__ q, int pitch,
-                           const double2 *__restrict__ trig, double *__restrict__ image, int n,
-                           int A, int D, double half_n, double half_d, double scale)
+                           const longlong2 *__restrict__ trig_fx, double *__restrict__ image,
+                           int n, int A, int D, long long half_d_fx, int S, double scale)
 {
-    constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52
     const int c = blockIdx.x * 16 + (threadIdx.x & 15);
     const int r0 = blockIdx.y * 16 + (threadIdx.x >> 4);
-    const double x = (double)c - half_n;
-    const double y0 = (double)r0 - half_n;
-    const double off = half_d - 0.5;
+    const long long X2 = 2LL * c - (n - 1);
+    const long long Y2 = 2LL * r0 - (n - 1);
+    const unsigned long long frac_mask = (1ULL << S) - 1ULL;
+    const int to_mantissa = 52 - S;
+    constexpr unsigned long long kOne = 0x3FF0000000000000ULL;  // 1.0
     double acc[kBp64Rows];
 #pragma unroll
     for (int j = 0; j < kBp64Rows; ++j) acc[j] = 0.0;
     for (int i = 0; i < A; ++i) {
-        const double2 cs = __ldg(&trig[i]);
+        const longlong2 cs = __ldg(&trig_fx[i]);
         const double2 *row = reinterpret_cast<const double2 *>(q + (size_t)i * pitch);
-        const double dv = (double)(16 / kBp64Rows) * cs.y;
-        double v = fma(x, cs.x, fma(y0, cs.y, off));
+        const long long du = (long long)(2 * (16 / kBp64Rows)) * cs.y;
+        long long u = X2 * cs.x + Y2 * cs.y + half_d_fx;
 #pragma unroll
         for (int j = 0; j < kBp64Rows; ++j) {
-            if (j > 0) v += dv;
-            const double t = v + kShift;
-            const int p = __double2loint(t) + 1;  // pair of bin floor(u)
-            const double w = v - (t - kShift);
+            if (j > 0) u += du;
+            const int p = (int)(u >> S) + 1;  // pair of bin floor(u)
+            const double f1 = __longlong_as_double(
+                (long long)(kOne | (((unsigned long long)u & frac_mask) << to_mantissa)));
             if ((unsigned)p <= (unsigned)D) {
-                const double2 ms = __ldg(&row[p]);
-                acc[j] += fma(w, ms.y, ms.x);
+                const double2 ad = __ldg(&row[p]);
+                acc[j] += fma(f1, ad.y, ad.x);
             }
         }
     }
@@ -243,9 +248,9 @@ cudaError_t launch_filter_fft_f64(const Plan &p, const double *sino, int ld, dou
 cudaError_t launch_backproject_f64(const Plan &p, const double *q, double *image, cudaStream_t s)
 {
     dim3 grid((p.n + 15) / 16, (p.n + 15) / 16);
-    backproject_f64_kernel<<<grid, kBp64Threads, 0, s>>>(q, p.pitch, p.d_trig64, image, p.n, p.A, p.D,
-                                                0.5 * (double)(p.n - 1), 0.5 * (double)(p.D - 1),
-                                                p.scale64);
+    backproject_f64_kernel<<<grid, kBp64Threads, 0, s>>>(q, p.pitch, p.d_trig_fx, image, p.n,
+                                                          p.A, p.D, p.half_d_fx, p.fx_shift,
+                                                          p.scale64);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,37 @@ def test_dynamic_work_handout_recomputes_every_tile(fbp):
         assert np.array_equal(im.cpu().numpy(), w)
 
 
+def test_concurrent_batches_on_two_streams(fbp):
+    """Two batches over the same plans (own buffers and work counters) launched
+    on two streams without synchronising between them: their persistent
+    launches share the GPU and hand out work independently, and every image
+    is the one its slice gets alone."""
+    import torch
+    specs = small_uneven_specs(10, seed=37)
+    plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det, filter=s.filter) for s in specs]
+    sinos_a = [_sino(s) for s in specs]
+    sinos_b = [(-0.5 * t).contiguous() for t in sinos_a]
+    want_a = [_alone(fbp, p, t) for p, t in zip(plans, sinos_a)]
+    want_b = [_alone(fbp, p, t) for p, t in zip(plans, sinos_b)]
+    ba, bb = fbp.Batch(plans, sinos_a), fbp.Batch(plans, sinos_b)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for im in ba.images + bb.images:
+            im.fill_(float("nan"))
+        torch.cuda.synchronize()
+        ba.launch(sa)
+        bb.launch(sb)
+        ba.launch(sa)
+        torch.cuda.synchronize()
+        ba.status()
+        bb.status()
+        for w, im in zip(want_a, ba.images):
+            assert np.array_equal(im.cpu().numpy(), w)
+        for w, im in zip(want_b, bb.images):
+            assert np.array_equal(im.cpu().numpy(), w)
+
+
 def test_batch_mixes_kernel_configurations(fbp):
     """Slices whose plans pick different kernels (tile shape, FP16 pairs, Kahan)
     share one batch; each still equals its own alone result bit for bit."""
