@@ -220,7 +220,10 @@ enum { FBP_BATCH_FILTER = 1, FBP_BATCH_BACKPROJECT = 2 };
 fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int n,
                                  const fbp_batch_io *io, int parts, fbp_stream_t stream);
 
-/* Enqueue the whole batch on `stream` (one graph launch). */
+/* Enqueue the whole batch on `stream` (one graph launch).  A batch's launches
+ * and fbp_batch_run_host calls share its buffers and the work counters of its
+ * backprojection launches: the caller orders them (one stream, or events);
+ * different batches may run concurrently. */
 fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream);
 
 /* Number of kernel launches one fbp_batch_launch performs (the kernel nodes of
@@ -236,8 +239,8 @@ fbp_status fbp_batch_kernel_count(fbp_batch_t batch, int *count);
  * six chunks, pipelined: the sinogram copies run on one internal stream, the
  * image copies on another, the compute alternately on `stream` and a third
  * internal stream, so that chunk c+1 comes in and chunk c-1 goes out while
- * chunk c computes, and consecutive chunks' kernels overlap.  One copy per slice and
- * direction; host buffers should be pinned for the copies to be asynchronous.
+ * chunk c computes, and consecutive chunks' kernels overlap.  One copy per slice
+ * and direction; host buffers should be pinned for the copies to be asynchronous.
  * The work starts after what is already on `stream` and `stream` waits for the
  * last image copy, so synchronising `stream` (or an event recorded on it after
  * this call) makes every image readable.  Results equal those of
