@@ -109,13 +109,13 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 namespace fbp {
 
 // Every slice's filter, then one persistent backprojection launch per kernel
-// configuration over the tiles of all slices of that configuration (slices
-// with the most angles first).  Launch-only: no allocation, no synchronisation.
-// `sched` holds n_sched work counters (two ints each, zero); the k-th
-// backprojection launch takes counter k and hands out its items dynamically,
-// launches beyond them stride statically.
+// configuration and item size over the tiles of all slices of that
+// configuration (slices with the most angles first).  The k-th backprojection
+// launch takes work counter k of `sched` and hands out its items dynamically;
+// launches beyond the n_sched counters stride statically.
 cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
-                         int *status, cudaStream_t s, int *sched, int n_sched)
+                         int *status, cudaStream_t s, int *sched, int n_sched,
+                         const BpFork *fork)
 {
     if (parts & FBP_BATCH_FILTER) {
         // FFT-route slices: one launch over all their row pairs
@@ -161,6 +161,13 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
     }
     std::unique_ptr<BpLaunch<kBpMaxSlices>> L(new BpLaunch<kBpMaxSlices>());
     int launches = 0;
+    bool forked = false;
+    if (fork != nullptr) {
+        cudaError_t e = cudaEventRecord(fork->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->side, fork->fork, 0);
+        if (e != cudaSuccess) return e;
+        forked = true;
+    }
     for (auto &kv : by_cfg) {
         std::vector<int> members = kv.second;
         std::stable_sort(members.begin(), members.end(),
@@ -222,10 +229,18 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
                 ++launches;
                 BpConfig c = cfg;
                 c.group = group;
-                cudaError_t e = launch_backproject_batch(*L, c, 0, s);
+                const bool on_side = forked && group == 1;
+                cudaError_t e = launch_backproject_batch(*L, c, 0, on_side ? fork->side : s);
                 if (e != cudaSuccess) return e;
             }
         }
+    }
+    if (forked) {
+        // the main stream waits for the side stream (also when it ran nothing,
+        // so a captured fork always joins)
+        cudaError_t e = cudaEventRecord(fork->join, fork->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->join, 0);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -317,18 +332,26 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
         return FBP_ERR_OUT_OF_MEMORY;
     }
 
-    // Capture the whole batch once into a graph on a private stream.
+    // Capture the whole batch once into a graph on a private stream, the
+    // single-slice backprojection launches on a forked branch.
     cudaStream_t cs = nullptr;
+    BpFork fork = {nullptr, nullptr, nullptr};
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fork.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork.join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = enqueue_many(b->plans.data(), b->io.data(), n, parts, b->d_status, cs,
-                                      b->d_sched, kSchedPerSet);
+                                      b->d_sched, kSchedPerSet, &fork);
         cudaError_t ee = cudaStreamEndCapture(cs, &b->graph);
         e = (le != cudaSuccess) ? le : ee;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (cs) cudaStreamDestroy(cs);
+    if (fork.side) cudaStreamDestroy(fork.side);
+    if (fork.fork) cudaEventDestroy(fork.fork);
+    if (fork.join) cudaEventDestroy(fork.join);
     if (e != cudaSuccess) {
         free_batch(b);
         set_error("fbp_batch_build: graph capture: %s", cudaGetErrorString(e));

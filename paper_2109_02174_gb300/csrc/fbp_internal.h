@@ -77,6 +77,25 @@ bool encode_pairs_map(const Plan &p, const void *q, CUtensorMap *out);
 bool encode_rows_map_3d(const void *q, int row_floats, int pitch, int rows, int planes,
                         int box_x, int box_y, CUtensorMap *out);
 
+// A second stream for enqueue_many: when given, the single-slice
+// backprojection launches run on `side` (after `fork`, recorded on the main
+// stream once the filters are enqueued) beside the two-slice launches, and the
+// main stream waits for `join` at the end, so one launch's last work items
+// and the other's overlap.
+struct BpFork {
+    cudaStream_t side;
+    cudaEvent_t fork;
+    cudaEvent_t join;
+};
+
+// Every slice's filter, then the persistent backprojection launches over all
+// slices' tiles (batch.cu).  `sched`: n_sched work counters (two ints each,
+// zero) for the backprojection launches in order; launches beyond them
+// stride.  Launch-only: no allocation, no synchronisation.
+cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
+                         int *status, cudaStream_t s, int *sched, int n_sched,
+                         const BpFork *fork = nullptr);
+
 // Filter launchers: write the (mid, slope) pairs of every row (see fbp.h).
 cudaError_t launch_filter_direct(const Plan &p, const float *sino, int ld, void *q,
                                  cudaStream_t s);

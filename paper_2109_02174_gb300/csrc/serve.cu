@@ -31,11 +31,6 @@
 
 #include "fbp_internal.h"
 
-namespace fbp {
-cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n, int parts,
-                         int *status, cudaStream_t s, int *sched, int n_sched);
-}  // namespace fbp
-
 using namespace fbp;
 
 namespace {
