@@ -54,6 +54,13 @@ constexpr size_t kSmemBudget = 200 * 1024;
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: x + kMagic holds round(x) in its low bits
 constexpr int kMagicLow = 0x4B400000;
 
+__device__ __forceinline__ float2 lds_f2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
 struct FdkPrm {
     float c, s, uc, tc;  // cos b, sin b, U_c, t_c
     float kuo, kvo;      // centre's bin and row coordinate, relative to the window
@@ -232,7 +239,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float ds = fmaf(dx, P.c, dy * P.s);
             const float dt = fmaf(dy, P.c, -dx * P.s);
             const float U = P.uc - ds;
-            const float inv = 1.0f / (U * P.uc);
+            // fast reciprocal (about 2 ulp): the window offsets it scales are
+            // tens of bins, so it moves a sample by ~1e-5 bins; IEEE division
+            // here cost 8% of the reconstruction
+            const float inv = __fdividef(1.0f, U * P.uc);
             const float ku = fmaf(g.Ru * fmaf(dt, P.uc, P.tc * ds), inv, P.kuo);
             const float fk = floorf(ku);
             // window pair of the voxel's interval; kept inside the window
@@ -244,8 +254,13 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float v0 = fmaf(g.Rv * zc * ds, inv, P.kvo) - 0.5f;
             const float2 bz2 = make_float2(bz, bz), v02 = make_float2(v0, v0);
             const float2 W2 = make_float2(W, W);
-            const float2 *win =
-                reinterpret_cast<const float2 *>(bp + (size_t)(s * g.ch + k) * g.box_bytes) + b;
+            // shared address of window pair (row r, pair b): the rounded row
+            // coordinate's bits are r + kMagicLow, so with the offset folded
+            // into wb the address is wb + bits * row_bytes (32-bit wraparound
+            // cancels)
+            const uint32_t row_bytes = 8u * (uint32_t)wu;
+            const uint32_t wb = base + (uint32_t)((s * g.ch + k) * g.box_bytes) + 8u * (uint32_t)b -
+                                row_bytes * (uint32_t)kMagicLow;
 #pragma unroll
             for (int jj = 0; jj < kT / 2; ++jj) {
                 const float2 dz = make_float2((float)(2 * jj) - 0.5f * (kT - 1),
@@ -259,10 +274,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 // tile's eight corners (where a box's perspective image takes its
                 // extremes) with a row of margin each side, far beyond the FP32
                 // error of kv (checked by emulating every test geometry's indices)
-                const int r0 = __float_as_int(t.x) - kMagicLow;
-                const int r1 = __float_as_int(t.y) - kMagicLow;
-                const float2 m00 = win[r0 * wu], m01 = win[(r0 + 1) * wu];
-                const float2 m10 = win[r1 * wu], m11 = win[(r1 + 1) * wu];
+                const uint32_t a0 = wb + __float_as_uint(t.x) * row_bytes;
+                const uint32_t a1 = wb + __float_as_uint(t.y) * row_bytes;
+                const float2 m00 = lds_f2(a0), m01 = lds_f2(a0 + row_bytes);
+                const float2 m10 = lds_f2(a1), m11 = lds_f2(a1 + row_bytes);
                 const float2 q0 = make_float2(fmaf(wu_off, m00.y, m00.x), fmaf(wu_off, m10.y, m10.x));
                 const float2 q1 = make_float2(fmaf(wu_off, m01.y, m01.x), fmaf(wu_off, m11.y, m11.x));
                 const float2 d = __ffma2_rn(q0, kNeg1, q1);   // q1 - q0
