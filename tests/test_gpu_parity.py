@@ -324,6 +324,26 @@ def test_fp64_small_and_ragged(fbp, n, A, D, path):
     assert e_max <= FP64_REL
 
 
+@pytest.mark.parametrize("path", sorted(FP64_PATHS))
+@pytest.mark.parametrize("tau", [0.7, 1.6])
+def test_fp64_given_angles_and_spacing(fbp, path, tau):
+    """Unsorted caller-given angles over a full turn and a non-unit bin width
+    (the fixed-point coordinate's table scales cos/tau and sin/tau; at tau =
+    1.6 the detector is narrower than the image diagonal)."""
+    import torch
+    n, A, D = 80, 37, 75
+    th = np.random.default_rng(int(10 * tau)).uniform(0.0, 2.0 * np.pi, A)
+    P = np.random.default_rng(int(100 * tau)).normal(size=(A, D))
+    plan = fbp.Plan(n, A, D, angles=th, det_spacing=tau, filter=1, dtype=1,
+                    filter_path=FP64_PATHS[path])
+    got = plan.reconstruct(torch.from_numpy(P).cuda())
+    torch.cuda.synchronize()
+    plan.device_status()
+    ref = oracle.fbp(P, th, tau, 1, n, nthreads=NTHREADS)
+    e_max, _ = errors(got.cpu().numpy(), ref)
+    assert e_max <= FP64_REL
+
+
 def test_fp64_fft_route_is_the_default_and_matches_direct(fbp):
     """AUTO resolves to the FP64 FFT when its length fits; the two FP64 routes
     give the same filtered pairs to rounding (linear convolution either way)."""
