@@ -124,6 +124,27 @@ def cpu_fbp_time(specs, sinos, nthreads):
     return time.perf_counter() - t0
 
 
+def cpu_config_times(cores):
+    """The FP64 oracle once on the batched configuration's 64 uneven slices and
+    once on the large slice (2048^2, 2048 angles, 2899 bins), all host cores:
+    slices/s and Gupdates/s beside the GPU's."""
+    import oracle
+    out = {}
+    for name, specs in (("batched_uneven_64", synthetic.cfg_batch()),
+                        ("large_2048x2048x2899", [synthetic.cfg_large()])):
+        thetas = [synthetic.default_angles(s.n_angles) for s in specs]
+        sinos = [synthetic.sinogram(s, th).astype(np.float32).astype(np.float64)
+                 for s, th in zip(specs, thetas)]
+        t0 = time.perf_counter()
+        for s, th, sino in zip(specs, thetas, sinos):
+            oracle.fbp(sino, th, s.tau, s.filter, s.n_pix, nthreads=cores)
+        sec = time.perf_counter() - t0
+        out[name] = {"slices_per_s": len(specs) / sec,
+                     "gupdates_per_s": sum(s.updates for s in specs) / sec / 1e9,
+                     "seconds": sec}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -662,6 +683,8 @@ def run_ours(args, rank, world, local_rank):
         t1 = cpu_fbp_time([spec0], sample, 1)
         line["cpu_one_core"] = {"value": 1.0 / t1, "unit": "slices/s", "cores": 1,
                                 "kind": "oracle", "sample": "the same slice on one host core"}
+        if not args.no_configs:
+            line["cpu_baseline"]["configs"] = cpu_config_times(cores)
     for b in (full, bp_only, filt_only):
         b.close()
     if world == 1 and args.serve_seconds > 0:
