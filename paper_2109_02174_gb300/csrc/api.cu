@@ -436,15 +436,31 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         trig[(size_t)i] = make_double2(std::cos(theta[(size_t)i]) / det_spacing,
                                        std::sin(theta[(size_t)i]) / det_spacing);
     // Backprojection tile: the largest of 32x64, 32x32, 8x32 pixels whose
-    // detector window fits one TMA box (256 elements = 128 pairs), unless the
-    // options name one of them.
+    // detector window fits one TMA box (256 elements = 128 pairs) and that
+    // cuts the image into at least one tile per two SMs (else the smallest
+    // that fits), unless the options name one of them.  A tile alone on an SM
+    // runs up to twice as fast as two sharing one, so a single slice loses
+    // nothing while at most half the SMs idle, and smaller tiles cost more per
+    // pixel (8x32 about 1.7x 32x64 on a full GPU).  One slice, microseconds,
+    // 32x64 / 32x32 / 8x32: 256^2 x 180: 31.4 / 29.3 / 27.4; 256^2 x 720:
+    // 77.4 / 65.2 / 61.1; 384^2 x 360: 49.8 / 43.7 / 48.8; 512^2 x 720:
+    // 79.5 / 82.6 / 134.8; 1024^2 x 1440: 482 / 504 / 832.
     const int align = (o.q_storage == FBP_F16) ? 4 : 2;
     const int shapes[3][2] = {{4, 2}, {4, 1}, {1, 1}};
+    int sms = 0;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     int pick = -1;
-    for (int k = 0; k < 3 && pick < 0; ++k) {
+    for (int k = 0; k < 3; ++k) {
         const int tx = 8 * shapes[k][0], ty = 32 * shapes[k][1];
         if ((o.tile_x || o.tile_y) && (o.tile_x != tx || o.tile_y != ty)) continue;
-        if (window_pairs(trig, tx, ty, align) <= 128) pick = k;
+        if (window_pairs(trig, tx, ty, align) > 128) continue;
+        pick = k;
+        const long tiles = (long)((n_pix + tx - 1) / tx) * (long)((n_pix + ty - 1) / ty);
+        if (2 * tiles >= (long)sms) break;
     }
     if (pick < 0 && o.dtype == FBP_F64) pick = 0;  // the FP64 path has no tiles
     if (pick < 0) {
