@@ -284,7 +284,7 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
     # sampled alone-vs-mix check, bitwise
     equal = 0
     for rid, (g, ph, out) in check.items():
-        plan = fbp.Plan(g[0], g[1], g[2])
+        plan = fbp.Plan(g[0], g[1], g[2], tile_x=-1, tile_y=-1)  # the server's plan choice
         alone = plan.reconstruct(pool[g][ph].cuda())
         torch.cuda.synchronize()
         equal += int(torch.equal(alone.cpu(), out))

@@ -86,8 +86,11 @@ typedef struct {
                          else the direct convolution; FP64 plans have no tensor-core
                          route */
     int fft_len;      /* 0 = auto (next power of two >= 2*n_det-1) */
-    int tile_x;       /* 0 = auto; pixel tile of one backprojection work item */
-    int tile_y;       /* 0 = auto */
+    int tile_x;       /* pixel tile of one backprojection work item: 32x64, 32x32 or
+                         8x32; 0 = auto for one slice (the largest whose detector
+                         window fits and that leaves at most half the SMs idle);
+                         -1 = the largest that fits (for batches and waves) */
+    int tile_y;       /* 0 = auto, -1 = largest (with tile_x) */
     int angle_chunk;  /* angles staged per shared-memory window: 8, 16, 32; 0 = 32 */
     double i0;        /* 0 (default): the sinogram holds line integrals p.  > 0: it
                          holds measured intensities or photon counts I of rays with
@@ -263,9 +266,10 @@ fbp_status fbp_batch_destroy(fbp_batch_t batch);
  * and launches admitted requests as waves (copies in, every slice's filter,
  * one persistent backprojection over all their tiles, copies out) on up to
  * n_streams streams at once, so requests that arrive while others run are
- * batched and overlap on the device (continuous batching).  Each request's
- * image is bit-identical to fbp_reconstruct with a default plan of its
- * geometry.  Latency = submit to the end of its image copy. */
+ * batched and overlap on the device (continuous batching).  The server's
+ * plans take the largest backprojection tile that fits (tile_x = tile_y = -1),
+ * and each request's image is bit-identical to fbp_reconstruct with such a
+ * plan of its geometry.  Latency = submit to the end of its image copy. */
 typedef struct fbp_server_s *fbp_server_t;
 
 typedef struct {

@@ -438,7 +438,9 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     // Backprojection tile: the largest of 32x64, 32x32, 8x32 pixels whose
     // detector window fits one TMA box (256 elements = 128 pairs) and that
     // cuts the image into at least one tile per two SMs (else the smallest
-    // that fits), unless the options name one of them.  A tile alone on an SM
+    // that fits), unless the options name one of them or ask (-1) for the
+    // largest that fits (for batches and serving waves, where several slices
+    // fill the SMs and the largest tile costs least per pixel).  A tile alone on an SM
     // runs up to twice as fast as two sharing one, so a single slice loses
     // nothing while at most half the SMs idle, and smaller tiles cost more per
     // pixel (8x32 about 1.7x 32x64 on a full GPU).  One slice, microseconds,
@@ -453,12 +455,14 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
+    const bool largest = o.tile_x < 0 || o.tile_y < 0;
     int pick = -1;
     for (int k = 0; k < 3; ++k) {
         const int tx = 8 * shapes[k][0], ty = 32 * shapes[k][1];
-        if ((o.tile_x || o.tile_y) && (o.tile_x != tx || o.tile_y != ty)) continue;
+        if (!largest && (o.tile_x || o.tile_y) && (o.tile_x != tx || o.tile_y != ty)) continue;
         if (window_pairs(trig, tx, ty, align) > 128) continue;
         pick = k;
+        if (largest) break;
         const long tiles = (long)((n_pix + tx - 1) / tx) * (long)((n_pix + ty - 1) / ty);
         if (2 * tiles >= (long)sms) break;
     }

@@ -182,9 +182,15 @@ fbp_plan_t plan_for(fbp_server_s *s, const fbp_request &r)
     const GeomKey key(r.n_pix, r.n_angles, r.n_det, r.det_spacing, r.filter);
     auto it = s->plans.find(key);
     if (it != s->plans.end()) return it->second;
+    // The largest backprojection tile that fits (tile -1), not the one-slice
+    // default: a wave holds several requests and makes one launch per tile
+    // shape, and the largest tile costs least per pixel.
+    fbp_options o;
+    fbp_options_default(&o);
+    o.tile_x = o.tile_y = -1;
     fbp_plan_t p = nullptr;
     if (fbp_plan(&p, r.n_pix, r.n_angles, r.n_det, nullptr, r.det_spacing,
-                 (fbp_filter_type)r.filter, nullptr) != FBP_OK)
+                 (fbp_filter_type)r.filter, &o) != FBP_OK)
         return nullptr;
     s->plans[key] = p;
     return p;

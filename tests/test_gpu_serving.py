@@ -53,7 +53,8 @@ def _host(spec):
 
 def _alone(fbp, spec, sino_host):
     import torch
-    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det)
+    # the server's plans take the largest backprojection tile that fits
+    plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, tile_x=-1, tile_y=-1)
     out = plan.reconstruct(sino_host.cuda())
     torch.cuda.synchronize()
     return out.cpu().numpy()

@@ -101,3 +101,27 @@ def test_autotune_keeps_fixed_route_tile_and_chunk(fbp):
     base.angle_chunk = 32
     t2 = fbp.fbp_autotune(n, A, D, base=base, batch=2)
     assert (t2["tile_x"], t2["tile_y"], t2["angle_chunk"]) == (8, 32, 32)
+
+
+def test_default_tile_rule(fbp):
+    """An untuned plan takes the largest tile whose window fits and that cuts
+    the image into at least one tile per two SMs; tile -1 takes the largest
+    that fits.  The tile fixes the bits (the local coordinate's origin), so
+    each choice is identified by matching an explicitly tiled plan."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    spec = synthetic.SliceSpec(256, 90, synthetic.det_for(256), 6, seed=71)
+    sino = torch.from_numpy(synthetic.sinogram(spec).astype(np.float32)).cuda()
+
+    def img(**opt):
+        out = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, **opt).reconstruct(sino)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    by_tile = {t: img(tile_x=t[0], tile_y=t[1]) for t in ((32, 64), (32, 32), (8, 32))}
+    # 256^2: 32 tiles of 32x64, 64 of 32x32, 256 of 8x32
+    expect = (32, 64) if 2 * 32 >= sms else (32, 32) if 2 * 64 >= sms else (8, 32)
+    assert np.array_equal(img(), by_tile[expect])
+    assert np.array_equal(img(tile_x=-1, tile_y=-1), by_tile[(32, 64)])
+    assert not np.array_equal(by_tile[(32, 64)], by_tile[(8, 32)])
+
