@@ -67,27 +67,93 @@ def peaks():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """SM clock and clock-event reasons of one GPU, sampled every 5 ms from a
+    thread through NVML (read-only queries) while the timed region runs;
+    nvidia-smi every 10 ms if NVML cannot be loaded."""
+    PERIOD_S = 0.005
+    # nvmlClocksEventReason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"fbp_clocks_{os.getpid()}.csv")
+    def __init__(self, gpu_index: int, props=None):
         self.gpu = gpu_index
+        self.props = props
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.nvml = None
+        self.handle = None
+        self.max_mhz = None
+        self.path = os.path.join(tempfile.gettempdir(), f"fbp_clocks_{os.getpid()}.csv")
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            ok = False
+            p = self.props
+            if p is not None and hasattr(p, "pci_bus_id"):
+                bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) == 0
+            if not ok:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) == 0
+            if not ok:
+                return False
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+                self.max_mhz = float(mx.value)
+            self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.nvml, self.handle = lib, h
+            return True
+        except Exception:
+            return False
+
+    def _loop(self):
+        import ctypes
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        while not self.stop_flag:
+            if self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, ctypes.byref(clk)) == 0:
+                r = rs.value if self.reason_fn(self.handle, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((float(clk.value), int(r)))
+            time.sleep(self.PERIOD_S)
 
     def start(self):
+        import threading
+        self.samples = []
+        self.stop_flag = False
+        if self.nvml is not None or self._nvml_open():
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+            return
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "10"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=5)
+            self.thread = None
+            if not self.samples:
+                return None
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS.items()
+                              if r & bit})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(sm), "source": "nvml, 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -112,7 +178,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi, 10 ms"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -221,14 +287,25 @@ def _timed(fn, steps, stream, per_launch=False):
     return e0.elapsed_time(e1)
 
 
+SERVE_CHECK_EVERY = 100  # one request in 100 (1%) is checked against alone and the oracle
+
+
 def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40.0,
                 max_wave: int = 32, n_streams: int = 3):
     """Poisson arrivals (mean `rate`/s, exponential gaps from SplitMix64(5)) of
     slices with n in {256,512,768,1024}, A in {360,720,1440}, D = ceil(n sqrt2)+1,
-    noisy (I0 = 1e5).  Sinogram content comes from a pool of two seeded phantoms
-    per geometry (generating 10^4 distinct analytic sinograms would take longer
-    than the run); every request has its own pinned output slot."""
+    noisy (I0 = 1e5).  One request in 100 carries its own seeded sinogram
+    (phantom seed 50000 + r, noise seed 150000 + r) and its own output buffer;
+    it is compared bit for bit with its alone result and kept for the oracle
+    check (check_serving_sample, run last).  The other requests' sinograms come
+    from a pool of two seeded phantoms per geometry (generating 2 x 10^4
+    distinct analytic sinograms would take longer than the run); every request
+    has its own pinned output slot.  After the arrival run, the capacity: the
+    first 4000 requests submitted as fast as output slots free up, through the
+    server and, for the plain single-slice path, one fbp_reconstruct per
+    request with its host-to-device and device-to-host copies on one stream."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     count = int(seconds * rate)
     stream = synthetic.serving_stream(count, seed=5, rate=rate)
     geoms = sorted({(s.n_pix, s.n_angles, s.n_det) for _, s in stream})
@@ -240,6 +317,13 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
                                        i0=1e5, noise_seed=150000 + 97 * k + g[0] + g[1])
             pool[g].append(torch.from_numpy(synthetic.sinogram(spec).astype(np.float32))
                            .pin_memory())
+    sampled = [k for k in range(count) if k % SERVE_CHECK_EVERY == 0]
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        own = dict(zip(sampled, ex.map(
+            lambda k: synthetic.sinogram(stream[k][1]).astype(np.float32), sampled)))
+    own_pinned = {k: torch.from_numpy(v).pin_memory() for k, v in own.items()}
+    own_out = {k: torch.empty((stream[k][1].n_pix,) * 2, dtype=torch.float32).pin_memory()
+               for k in sampled}
     RING = 48
     rings = {n: [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in range(RING)]
              for n in sorted({g[0] for g in geoms})}
@@ -255,7 +339,6 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
     for g in geoms:
         server.warm(g[0], g[1], g[2])
     counters = {n: 0 for n in rings}
-    ids = []
     check = {}
     t0 = time.perf_counter()
     for k, (t, spec) in enumerate(stream):
@@ -270,23 +353,24 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
                 break
             if dt > 2e-4:
                 time.sleep(dt - 1e-4)
-        g = (n, spec.n_angles, spec.n_det)
-        sino = pool[g][k % 2]
-        if k % 997 == 0:  # sampled request: its own output buffer, kept for the check
-            out = torch.empty((n, n), dtype=torch.float32).pin_memory()
-            rid = server.submit(sino, out, n)
-            check[rid] = (g, k % 2, out)
+        if k in own_pinned:  # sampled request: own sinogram and output buffer
+            rid = server.submit(own_pinned[k], own_out[k], n)
+            check[k] = own_out[k]
         else:
-            rid = server.submit(sino, rings[n][slot], n)
+            g = (n, spec.n_angles, spec.n_det)
+            rid = server.submit(pool[g][k % 2], rings[n][slot], n)
             owner[n][slot] = rid
-        ids.append(rid)
     server.drain(300.0)
     st = server.stats()
-    # sampled alone-vs-mix check, bitwise
+    # the sampled requests against their alone results, bit for bit
+    plans = {}
     equal = 0
-    for rid, (g, ph, out) in check.items():
-        plan = fbp.Plan(g[0], g[1], g[2], tile_x=-1, tile_y=-1)  # the server's plan choice
-        alone = plan.reconstruct(pool[g][ph].cuda())
+    for k, out in check.items():
+        spec = stream[k][1]
+        g = (spec.n_pix, spec.n_angles, spec.n_det)
+        if g not in plans:
+            plans[g] = fbp.Plan(*g, tile_x=-1, tile_y=-1)  # the server's plan choice
+        alone = plans[g].reconstruct(own_pinned[k].cuda())
         torch.cuda.synchronize()
         equal += int(torch.equal(alone.cpu(), out))
     server.close()
@@ -311,6 +395,30 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
     t_sat = time.perf_counter() - t_sat
     sst = sat.stats()
     sat.close()
+    # the plain single-slice path on the same 4000 requests: per request the
+    # sinogram copy in, one fbp_reconstruct (default plan of its geometry), the
+    # image copy out, all on one stream
+    cs = torch.cuda.current_stream()
+    sp = int(cs.cuda_stream)
+    pplans = {g: fbp.Plan(*g) for g in geoms}
+    dsino = {g: torch.empty((g[1], g[2]), device="cuda") for g in geoms}
+    dimg = {g: torch.empty((g[0], g[0]), device="cuda") for g in geoms}
+    dws = {g: pplans[g].empty_workspace() for g in geoms}
+
+    def plain_request(k, spec):
+        g = (spec.n_pix, spec.n_angles, spec.n_det)
+        dsino[g].copy_(pool[g][k % 2], non_blocking=True)
+        fbp.fbp_reconstruct(pplans[g].handle, dsino[g].data_ptr(), g[2], dimg[g].data_ptr(),
+                            dws[g].data_ptr(), sp)
+        rings[g[0]][k % RING].copy_(dimg[g], non_blocking=True)
+    for g in geoms:  # first call per geometry outside the timing
+        plain_request(0, synthetic.SliceSpec(g[0], g[1], g[2], 1, 0))
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter()
+    for k, (_, spec) in enumerate(burst):
+        plain_request(k, spec)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t_plain
     upd = sum(s.updates for _, s in stream)
     sat_upd = sum(s.updates for _, s in burst)
     capacity = {"requests": sst["completed"], "seconds": t_sat,
@@ -318,8 +426,11 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
                 "gupdates_per_s": sat_upd / t_sat / 1e9,
                 "p50_ms": sst["p50_ms"], "p99_ms": sst["p99_ms"],
                 "max_waves_in_flight": sst["max_waves_in_flight"],
+                "plain_path_slices_per_s": len(burst) / t_plain,
+                "plain_path": "one fbp_reconstruct per request (default plan), sinogram "
+                              "copied in and image copied out, one stream, same 4000 requests",
                 "what": "the first 4000 requests of the mix, submitted without arrival gaps"}
-    return {
+    result = {
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
         "max_ms": st["max_ms"], "requests": st["completed"], "failed": st["failed"],
         "slices_per_s": st["completed"] / st["span_s"] if st["span_s"] else None,
@@ -328,10 +439,34 @@ def run_serving(fbp, seconds: float, rate: float = 2000.0, budget_gb: float = 40
         "admission_stalls": st["admission_stalls"], "waves": st["waves"],
         "max_waves_in_flight": st["max_waves_in_flight"],
         "peak_gb": st["peak_bytes"] / 2 ** 30, "budget_gb": budget_gb,
-        "bitwise_equal_to_alone": f"{equal}/{len(check)} sampled requests",
+        "bitwise_equal_to_alone": f"{equal}/{len(check)} sampled requests "
+                                  f"(1 in {SERVE_CHECK_EVERY}, own seeded sinograms)",
         "latency": "submit to the end of the image copy to pinned host memory",
         "capacity": capacity,
     }
+    sample = [(stream[k][1], own[k], check[k].numpy().copy()) for k in sorted(check)]
+    return result, sample
+
+
+def check_serving_sample(sample, cores):
+    """The sampled serving results against the FP64 oracle's whole images
+    (all host cores): how many meet the FP32 bars, and the worst errors."""
+    import oracle
+    ok, worst_max, worst_rmse = 0, 0.0, 0.0
+    t0 = time.perf_counter()
+    for spec, sino32, img in sample:
+        th = synthetic.default_angles(spec.n_angles)
+        ref = oracle.fbp(sino32.astype(np.float64), th, spec.tau, spec.filter, spec.n_pix,
+                         nthreads=cores)
+        scale = float(np.abs(ref).max())
+        err = img.astype(np.float64) - ref
+        e_max = float(np.abs(err).max()) / scale
+        e_rms = float(np.sqrt(np.mean(err ** 2))) / scale
+        ok += int(e_max <= 1e-4 and e_rms <= 2e-5)
+        worst_max, worst_rmse = max(worst_max, e_max), max(worst_rmse, e_rms)
+    return {"within_fp32_bars": f"{ok}/{len(sample)}", "worst_max_rel": worst_max,
+            "worst_rmse_rel": worst_rmse, "seconds": time.perf_counter() - t0,
+            "what": "every pixel of each sampled request against the FP64 oracle's image"}
 
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 rate (nominal; no measured figure on this pool)
@@ -410,7 +545,7 @@ def run_configs(fbp):
         img = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter,
                        **opt).reconstruct(s32)
         db, ss = fbp.quality(img, img64)
-        quality[name] = {"psnr_db": db, "ssim": ss}
+        quality[name] = {"psnr_db": db, "ssim": ss, "one_minus_ssim": 1.0 - ss}
     out["quality_vs_fp64_512x720x725"] = quality
     fp64_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2 / FP64_OPS_PER_UPDATE / 1e9
     out["fp64_512x720x725"] = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
@@ -434,6 +569,30 @@ def run_configs(fbp):
         filt()
         torch.cuda.synchronize()
         entry["filter_ms"][name] = _timed_flushed(filt, 5, stream, flush)
+    # the backprojection launch of the large slice alone (one slice, the
+    # default plan's tile), against the ALU figure and the shared-memory
+    # ceiling of the headline's roofline record
+    q_large = plan.filter(sino)
+    img_large = plan.empty_image()
+
+    def bp_large():
+        fbp.fbp_backproject(plan.handle, q_large.data_ptr(), img_large.data_ptr(), sp)
+    bp_large()
+    torch.cuda.synchronize()
+    bp_ms = _timed_flushed(bp_large, 10, stream, flush)
+    pk_l, pk_kind_l = peaks()
+    sms_l = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz_l = float(pk_l.get("sm_max_mhz", 2070.0))
+    peak_l = FP32_LANES_PER_SM * sms_l * mhz_l * 1e6 / OPS_PER_UPDATE / 1e9
+    smem_l = SMEM_UPDATES_PER_CLK_SM * sms_l * mhz_l / 1e3
+    ach_l = spec.updates / (bp_ms / 1e3) / 1e9
+    entry["roofline"] = {
+        "bound": "alu", "kernel": "bp_persistent_kernel (one slice, default plan)",
+        "achieved": ach_l, "peak": peak_l, "unit": "Gupdates/s", "frac": ach_l / peak_l,
+        "smem_ceiling": {"gupdates_per_s": smem_l, "frac": ach_l / smem_l},
+        "launch_ms": bp_ms, "updates_per_launch": spec.updates,
+        "traffic": None, "peak_basis": f"as the headline ({pk_kind_l} sm_max_mhz)"}
+    del q_large, img_large
     # the Lambert-Beer conversion fused into the filter's loads: the batched
     # filter of 64 float-vs-double slices from line integrals and from counts
     fb = synthetic.cfg_float_double()
@@ -583,7 +742,7 @@ def run_ours(args, rank, world, local_rank):
     full.status()
 
     # ---- timed region: K steps of the batched hot path (filter + backprojection)
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(local_rank, torch.cuda.get_device_properties(dev))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -686,8 +845,9 @@ def run_ours(args, rank, world, local_rank):
                                 "kind": "oracle", "sample": "the same slice on one host core"}
     for b in (full, bp_only, filt_only):
         b.close()
+    serve_sample = None
     if world == 1 and args.serve_seconds > 0:
-        line["serving"] = run_serving(fbp, args.serve_seconds)
+        line["serving"], serve_sample = run_serving(fbp, args.serve_seconds)
     if world == 1 and not args.no_uneven:
         line["batched_uneven"] = run_uneven(fbp)
     if world == 1 and not args.no_configs:
@@ -696,6 +856,9 @@ def run_ours(args, rank, world, local_rank):
         # last: tens of seconds on every host core, which also disturbed the
         # serving loop's latency when it ran just before it
         line["cpu_baseline"]["configs"] = cpu_config_times(os.cpu_count() or 1)
+    if serve_sample:
+        line["serving"]["oracle_check"] = check_serving_sample(serve_sample,
+                                                               os.cpu_count() or 1)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -348,7 +348,10 @@ fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
  *          with Gaussian window weights (sigma 1.5, normalised), C1 = (0.01 L)^2,
  *          C2 = (0.03 L)^2 (Wang, Bovik, Sheikh & Simoncelli 2004); L is
  *          dynamic_range, or the reference's max - min when dynamic_range <= 0;
- *          NaN when rows or cols < 11.
+ *          NaN when rows or cols < 11.  The local statistics are FP64 and each
+ *          window's value is formed through its distance from 1 (from the
+ *          local mean and variance of x - y), so near-identical images keep
+ *          1 - SSIM to the precision of their differences and SSIM <= 1.
  * Every sum is taken in a fixed order: the results are the same bits every run. */
 
 /* Device scratch fbp_quality needs for a rows x cols image, in *bytes. */
@@ -438,17 +441,21 @@ fbp_status fbp_fdk_status(fbp_fdk_plan_t plan);
  * Same result as fbp_reconstruct (same kernels, same bits); the filtered
  * sinogram goes to a 256-byte-aligned static device array of
  * FBP_STATIC_SCRATCH_BYTES compiled into the library instead of a caller
- * workspace.  The call makes no cudaMalloc, cudaFree or other allocating call;
- * the plan (whose tables fbp_plan allocated once, beforehand) is reused.
+ * workspace.  The call makes no cudaMalloc, cudaFree or other allocating call,
+ * and loads no code: fbp_plan, which the caller runs once beforehand, loads
+ * the plan's kernels and looks up the array's device address on its device
+ * (cudaGetSymbolAddress).  Under CUDA's lazy module loading (the default) the
+ * array becomes resident on a device at that first fbp_plan, not when the
+ * library is loaded, and stays until the process exits.  Each fbp_plan
+ * refreshes the address, so plans made after a cudaDeviceReset use the new one.
  *   sino, ld_sino, image  as for fbp_reconstruct (device, caller-owned)
  * Errors: FBP_ERR_BUDGET when the plan's workspace (fbp_workspace_bytes)
- * exceeds FBP_STATIC_SCRATCH_BYTES; otherwise as fbp_reconstruct.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  Every call on a device shares the one array and it keeps the last
- * call's contents (nothing in it needs to start at zero: the filter writes
- * every element the backprojection reads), so calls whose GPU work overlaps --
- * on different streams, or from different threads -- race on it; order them on
+ * exceeds FBP_STATIC_SCRATCH_BYTES; FBP_ERR_CUDA if the address could not be
+ * looked up when the plan was made; otherwise as fbp_reconstruct.
+ * Every call on a device shares the one array and it keeps the last call's
+ * contents (nothing in it needs to start at zero: the filter writes every
+ * element the backprojection reads), so calls whose GPU work overlaps -- on
+ * different streams, or from different threads -- race on it; order them on
  * one stream or serialise them.
  */
 fbp_status fbp_reconstruct_static(fbp_plan_t plan, const void *sino, int ld_sino, void *image,
@@ -457,6 +464,37 @@ fbp_status fbp_reconstruct_static(fbp_plan_t plan, const void *sino, int ld_sino
 /* Read and clear the plan's device status word (synchronises the device):
  * FBP_OK, or FBP_ERR_TIMEOUT if a bounded device wait ran out since the last read. */
 fbp_status fbp_device_status(fbp_plan_t plan);
+
+/* ------------------------------------------------------------------ bounded waits
+ * The pipelined kernels (backprojection, tensor-core filter, FDK
+ * backprojection) wait on shared-memory barriers; every such wait gives up
+ * after a limit, records FBP_ERR_TIMEOUT in the status word of the plan, batch
+ * or FDK plan that launched it (fbp_device_status, fbp_batch_status,
+ * fbp_fdk_status), and the kernel returns with nothing in flight, leaving the
+ * CUDA context usable.  The paper has no counterpart: this is the library's
+ * failure detection.  A batch whose status reports a timeout also has its
+ * work counters reset by fbp_batch_status, so its next launch is complete. */
+
+/* Set the wait limit, in seconds, for kernels that start after the call on the
+ * current device (kernels of CUDA graphs read it when they run, so graphs
+ * captured earlier follow it too).  0 restores the default of 2 s; otherwise
+ * 1e-6 .. 3600.  Writes device memory (synchronous).  FBP_ERR_INVALID_ARG for
+ * a value out of range, FBP_ERR_CUDA without a usable device. */
+fbp_status fbp_set_wait_limit(double seconds);
+
+/* TEST ONLY (fault injection without a GPU fault).  With kernel set, the first
+ * CTA of every later launch of that kernel kind on the current device
+ * withholds the arrival of one pipeline stage (`stage`: the CTA's stage fill
+ * count, from 0) and issues no copy for it, so the waits on that stage run out
+ * after the wait limit and the launch reports FBP_ERR_TIMEOUT; the image of
+ * that launch is then incomplete.  FBP_TEST_WITHHOLD_NONE (stage ignored)
+ * switches it off.  Read by kernels when they run, like the wait limit. */
+enum {
+    FBP_TEST_WITHHOLD_NONE = 0,
+    FBP_TEST_WITHHOLD_BACKPROJECT = 1, /* persistent backprojection (single slice and batches) */
+    FBP_TEST_WITHHOLD_FILTER_TC = 2    /* tensor-core Toeplitz filter (loader warps' arrival) */
+};
+fbp_status fbp_test_withhold_arrival(int kernel, int stage);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char *fbp_last_error(void);

@@ -126,6 +126,8 @@ _SIGS = {
     "fbp_batch_run_host": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "fbp_batch_status": [_P],
     "fbp_batch_destroy": [_P],
+    "fbp_set_wait_limit": [ctypes.c_double],
+    "fbp_test_withhold_arrival": [_I, _I],
 }
 
 
@@ -228,6 +230,20 @@ def fbp_reconstruct_static(plan: int, sino_ptr: int, ld_sino: int, image_ptr: in
 
 def fbp_device_status(plan: int):
     _check(load_library().fbp_device_status(plan))
+
+
+FBP_TEST_WITHHOLD_NONE, FBP_TEST_WITHHOLD_BACKPROJECT, FBP_TEST_WITHHOLD_FILTER_TC = 0, 1, 2
+
+
+def fbp_set_wait_limit(seconds: float):
+    """Limit of the kernels' bounded device waits on the current device (0 = 2 s)."""
+    _check(load_library().fbp_set_wait_limit(float(seconds)))
+
+
+def fbp_test_withhold_arrival(kernel: int, stage: int = 0):
+    """Test-only: the first CTA of later launches of `kernel` withholds the
+    arrival of pipeline stage `stage` (FBP_TEST_WITHHOLD_NONE switches it off)."""
+    _check(load_library().fbp_test_withhold_arrival(int(kernel), int(stage)))
 
 
 def fbp_batch_build(plans, ios, parts: int = FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT) -> int:

@@ -4,12 +4,14 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "backproject.cuh"
 #include "fbp_internal.h"
 #include "filter_tc.cuh"
+#include "ptx.cuh"
 
 namespace fbp {
 
@@ -596,6 +598,22 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         free_plan(p);
         return cuda_fail(e, "fbp_plan: table upload");
     }
+    // Load (CUDA loads modules lazily) the kernels of the plan's single-slice
+    // path now, so that fbp_filter, fbp_backproject, fbp_reconstruct and
+    // fbp_reconstruct_static load no code and allocate nothing when called.
+    if (p->dtype == FBP_F64) {
+        e = prepare_fp64(*p);
+    } else {
+        if (p->filter_path == FBP_PATH_FFT) e = prepare_filter_fft(*p);
+        else if (p->filter_path == FBP_PATH_TOEPLITZ_TC) e = prepare_filter_tc(*p);
+        else e = prepare_filter_direct(*p);
+        if (e == cudaSuccess) e = prepare_backproject(*p);
+    }
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "fbp_plan: kernel preparation");
+    }
+    static_scratch_setup(p->device);
     *out = reinterpret_cast<fbp_plan_t>(p);
     return FBP_OK;
 }
@@ -636,6 +654,7 @@ fbp_status fbp_plan_query(fbp_plan_t plan, int *q_pitch, int *fft_len, int *filt
 fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filtered,
                       fbp_stream_t stream)
 {
+    NvtxRange range("fbp_filter");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     fbp_status st = check_call(p, "fbp_filter", {sino, filtered});
     if (st != FBP_OK) return st;
@@ -663,6 +682,7 @@ fbp_status fbp_filter(fbp_plan_t plan, const void *sino, int ld_sino, void *filt
 fbp_status fbp_backproject(fbp_plan_t plan, const void *filtered, void *image,
                            fbp_stream_t stream)
 {
+    NvtxRange range("fbp_backproject");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     fbp_status st = check_call(p, "fbp_backproject", {filtered, image});
     if (st != FBP_OK) return st;
@@ -719,5 +739,73 @@ fbp_status fbp_device_status(fbp_plan_t plan)
 }
 
 const char *fbp_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+namespace {
+
+// Host copies of the wait settings per device (written whole to every
+// translation unit's device copy on each change).
+constexpr int kHookDevices = 64;
+std::mutex g_hook_mu;
+fbp::WaitHook g_hooks[kHookDevices];
+
+fbp_status push_hook(const char *fn, int dev)
+{
+    cudaError_t e = set_wait_hook_backproject(g_hooks[dev]);
+    if (e == cudaSuccess) e = set_wait_hook_filter_tc(g_hooks[dev]);
+    if (e == cudaSuccess) e = set_wait_hook_fdk(g_hooks[dev]);
+    return e == cudaSuccess ? FBP_OK : cuda_fail(e, fn);
+}
+
+fbp_status hook_device(const char *fn, int *dev)
+{
+    if (cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= kHookDevices) {
+        set_error("%s: no usable current CUDA device", fn);
+        return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fbp_status fbp_set_wait_limit(double seconds)
+{
+    if (!std::isfinite(seconds) || seconds < 0.0 || (seconds > 0.0 && seconds < 1e-6) ||
+        seconds > 3600.0) {
+        set_error("fbp_set_wait_limit: %g s is not 0 (default) or in [1e-6, 3600]", seconds);
+        return FBP_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    fbp_status st = hook_device("fbp_set_wait_limit", &dev);
+    if (st != FBP_OK) return st;
+    std::lock_guard<std::mutex> lock(g_hook_mu);
+    g_hooks[dev].limit_ns = (unsigned long long)std::llround(seconds * 1e9);
+    return push_hook("fbp_set_wait_limit", dev);
+}
+
+fbp_status fbp_test_withhold_arrival(int kernel, int stage)
+{
+    if (kernel != FBP_TEST_WITHHOLD_NONE && kernel != FBP_TEST_WITHHOLD_BACKPROJECT &&
+        kernel != FBP_TEST_WITHHOLD_FILTER_TC) {
+        set_error("fbp_test_withhold_arrival: unknown kernel kind %d", kernel);
+        return FBP_ERR_INVALID_ARG;
+    }
+    if (kernel != FBP_TEST_WITHHOLD_NONE && stage < 0) {
+        set_error("fbp_test_withhold_arrival: stage %d < 0", stage);
+        return FBP_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    fbp_status st = hook_device("fbp_test_withhold_arrival", &dev);
+    if (st != FBP_OK) return st;
+    std::lock_guard<std::mutex> lock(g_hook_mu);
+    g_hooks[dev].kind = kernel == FBP_TEST_WITHHOLD_BACKPROJECT ? kWithholdBackproject
+                        : kernel == FBP_TEST_WITHHOLD_FILTER_TC ? kWithholdFilterTc
+                                                                : kWithholdNone;
+    g_hooks[dev].stage = kernel == FBP_TEST_WITHHOLD_NONE ? -1 : stage;
+    return push_hook("fbp_test_withhold_arrival", dev);
+}
 
 }  // extern "C"

@@ -29,8 +29,18 @@
 //
 // Every pixel sums its angles in order 0..A-1 in registers: no atomics, no
 // cross-CTA reduction, the same bits on every run and in every batch.
+//
+// Every mbarrier wait is bounded (the run-time limit of WaitHook).  A consumer
+// whose wait runs out records FBP_ERR_TIMEOUT and leaves; a producer whose
+// wait for a free stage runs out records it, waits (bounded again) for the
+// TMA loads it issued into the ring to land, and leaves, so no bulk copy is
+// in flight when the CTA exits.  For tests, the first CTA can withhold one
+// stage's arrival (no TMA issued for it), which makes those waits run out.
+#include <cstring>
+
 #include "backproject.cuh"
 #include "ptx.cuh"
+#include "waithook.cuh"
 
 namespace fbp {
 namespace {
@@ -153,6 +163,8 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     };
     // single-slice launches (MAXS = 1) always stride: no counter code in them
     const bool dyn = MAXS > 1 && P.sched != nullptr;
+    const WaitHook hook = g_wait_hook;
+    const unsigned long long lim = wait_limit_ns(hook);
 
     if (warp == NCW) {
         // ------------------------------------------------------------ producer
@@ -162,18 +174,31 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
         // every item carries its index for the consumers, and a stage
         // carrying -1 ends their loop) or, without one, by striding (b,
         // b + grid, ...), which the consumers follow on their own.
+        const int withhold = withheld_stage(hook, kWithholdBackproject, blockIdx.x == 0);
         auto wait_empty = [&](uint32_t i) -> bool {
             const uint32_t use = i / NSTAGE;
             bool ok = true;
-            if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * (i % NSTAGE), (use - 1) & 1u);
+            if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * (i % NSTAGE), (use - 1) & 1u, lim);
             return __all_sync(0xffffffffu, ok);
+        };
+        // A wait for stage i's slot ran out: record it, then let the loads
+        // issued into the ring (stages i - NSTAGE .. i - 1, each its latest
+        // phase) land before leaving.
+        auto give_up = [&](uint32_t i) {
+            if (lane == 0) {
+                *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                for (uint32_t j = (i >= (uint32_t)NSTAGE ? i - NSTAGE : 0u); j < i; ++j)
+                    if ((int)j != withhold)
+                        (void)mbar_wait_bounded(full0 + 8u * (j % NSTAGE), (j / NSTAGE) & 1u, lim);
+            }
+            __syncwarp();
         };
         uint32_t it = 0;
         int item = blockIdx.x;
         for (;;) {
             if (!dyn && item >= P.n_items) return;  // the consumers stride too
             if (!wait_empty(it)) {
-                if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                give_up(it);
                 return;
             }
             if (dyn) {
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             for (int cc = 0; cc < nch; ++cc, ++it) {
                 const int s = (int)(it % NSTAGE);
                 if (cc > 0 && !wait_empty(it)) {
-                    if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
+                    give_up(it);
                     return;
                 }
                 const int a0 = cc * CH;
@@ -224,14 +249,16 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                                                      __int_as_float(item));
                 }
                 __syncwarp();
-                if (lane == 0) {
+                // (tests only: a withheld stage gets neither its arrival nor its loads)
+                const bool fill = (int)it != withhold;
+                if (lane == 0 && fill) {
                     const uint32_t bar = full0 + 8u * s;
                     mbar_arrive_expect_tx(bar, (uint32_t)(G * na * S.wp * TR::kBytes));
                 }
                 __syncwarp();
                 // each lane issues its own angle's load(s) (x in elements of PairT);
                 // slice g of the item lands in rows g*CH .. g*CH + CH-1 of the stage
-                if (lane < na) {
+                if (lane < na && fill) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         tma_load_2d(base_addr + (uint32_t)(s * L.stage + (g * CH + lane) * L.row),
@@ -255,7 +282,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     const float2 kNeg1 = make_float2(-1.0f, -1.0f);
 
     auto wait_full = [&](uint32_t i) -> bool {
-        const bool ok = mbar_wait_bounded(full0 + 8u * (i % NSTAGE), (i / NSTAGE) & 1u);
+        const bool ok = mbar_wait_bounded(full0 + 8u * (i % NSTAGE), (i / NSTAGE) & 1u, lim);
         return __all_sync(0xffffffffu, ok);
     };
     uint32_t it = 0;
@@ -374,6 +401,7 @@ cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (grid_limit < 0) return cudaSuccess;  // preparation only: the kernel is loaded
     int grid = sms * (per_sm > 0 ? per_sm : 1);
     if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
     if (grid > P.n_items) grid = P.n_items;
@@ -420,9 +448,19 @@ cudaError_t dispatch(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit,
 
 }  // namespace
 
+cudaError_t set_wait_hook_backproject(const WaitHook &h) { return write_wait_hook(h); }
+
 cudaError_t launch_backproject(const BpLaunch<1> &P, const BpConfig &c, cudaStream_t s)
 {
     return dispatch<1>(P, c, 0, s);
+}
+
+cudaError_t prepare_backproject(const Plan &p)
+{
+    BpLaunch<1> L;
+    std::memset(&L, 0, sizeof L);
+    L.wp_max = p.bp_wp;
+    return dispatch<1>(L, bp_config(p), -1, nullptr);
 }
 
 cudaError_t launch_backproject_batch(const BpLaunch<kBpMaxSlices> &P, const BpConfig &c,

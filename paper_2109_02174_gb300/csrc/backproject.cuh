@@ -62,6 +62,9 @@ struct BpConfig {
     int group;        // slices per work item: 1, or 2 (same plan, not Kahan)
 };
 
+// The kernel configuration of a plan's slices (api.cu).
+BpConfig bp_config(const Plan &p);
+
 cudaError_t launch_backproject(const BpLaunch<1> &P, const BpConfig &c, cudaStream_t s);
 cudaError_t launch_backproject_batch(const BpLaunch<kBpMaxSlices> &P, const BpConfig &c,
                                      int grid_limit, cudaStream_t s);

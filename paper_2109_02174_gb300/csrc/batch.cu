@@ -365,6 +365,7 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
 fbp_status fbp_reconstruct_many(const fbp_plan_t *plans, int n, const fbp_batch_io *io,
                                 fbp_stream_t stream)
 {
+    NvtxRange range("fbp_reconstruct_many");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         set_error("fbp_reconstruct_many: no current CUDA device");
@@ -386,6 +387,7 @@ fbp_status fbp_reconstruct_many(const fbp_plan_t *plans, int n, const fbp_batch_
 
 fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream)
 {
+    NvtxRange range("fbp_batch_launch (graph replay)");
     fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
     if (b == nullptr) {
         set_error("fbp_batch_launch: batch is NULL");
@@ -402,6 +404,7 @@ fbp_status fbp_batch_launch(fbp_batch_t batch, fbp_stream_t stream)
 fbp_status fbp_batch_run_host(fbp_batch_t batch, const void *const *host_sinos,
                               void *const *host_images, fbp_stream_t stream)
 {
+    NvtxRange range("fbp_batch_run_host");
     fbp_batch_s *b = reinterpret_cast<fbp_batch_s *>(batch);
     if (b == nullptr || host_sinos == nullptr || host_images == nullptr) {
         set_error("fbp_batch_run_host: NULL argument");

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -10,6 +11,17 @@
 #include "fbp.h"
 
 namespace fbp {
+
+// NVTX range over a host scope (the enqueue of a filter, a backprojection, a
+// graph replay, a serving admission): visible in a profiler's timeline,
+// inert otherwise (the header-only NVTX library does nothing until a tool
+// attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxFftLen = 8192;    // FP32 FFT route: two N-point complex buffers in shared memory
 constexpr int kMaxFftLen64 = 4096;  // FP64 FFT route: two N-point double2 buffers (128 KB)
@@ -121,5 +133,25 @@ size_t filter_fft_f64_smem_bytes(int N);
 
 cudaError_t launch_radon_forward_f32(const Plan &p, const float *image, float *sino,
                                      cudaStream_t s);
+
+// Writers of each translation unit's copy of the wait settings (WaitHook,
+// ptx.cuh) on the current device.
+struct WaitHook;
+cudaError_t set_wait_hook_backproject(const WaitHook &h);
+cudaError_t set_wait_hook_filter_tc(const WaitHook &h);
+cudaError_t set_wait_hook_fdk(const WaitHook &h);
+
+// Kernel preparation at plan time (each loads, under CUDA's lazy module
+// loading, the kernels the plan's single-slice path launches, and sets their
+// shared-memory limits), so later calls load no code.
+cudaError_t prepare_filter_fft(const Plan &p);
+cudaError_t prepare_filter_direct(const Plan &p);
+cudaError_t prepare_filter_tc(const Plan &p);
+cudaError_t prepare_backproject(const Plan &p);
+cudaError_t prepare_fp64(const Plan &p);
+
+// Device address of fbp_reconstruct_static's scratch array on the current
+// device, looked up at plan time (noalloc.cu).
+void static_scratch_setup(int device);
 
 }  // namespace fbp

@@ -38,6 +38,7 @@
 
 #include "fbp_internal.h"
 #include "ptx.cuh"
+#include "waithook.cuh"
 
 namespace fbp {
 
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const FdkPrm *pt = prm + (size_t)tile * g.A;
     const int nch = (g.A + g.ch - 1) / g.ch;
     const uint32_t box_payload = (uint32_t)(g.wv * 2 * g.wu * 4);
+    const unsigned long long lim = wait_limit_ns(g_wait_hook);
 
     if (warp == kConsumerWarps) {
         // ---------------------------------------------------- TMA producer
@@ -187,9 +189,16 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int s = c % kStages;
             const uint32_t use = (uint32_t)(c / kStages);
             bool ok = true;
-            if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * s, (use - 1) & 1u);
+            if (use > 0) ok = mbar_wait_bounded(empty0 + 8u * s, (use - 1) & 1u, lim);
             if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) *reinterpret_cast<volatile int *>(g.status) = FBP_ERR_TIMEOUT;
+                if (lane == 0) {
+                    *reinterpret_cast<volatile int *>(g.status) = FBP_ERR_TIMEOUT;
+                    // the loads already issued (each stage's latest phase) land first
+                    for (int j = (c > kStages ? c - kStages : 0); j < c; ++j)
+                        (void)mbar_wait_bounded(full0 + 8u * (j % kStages),
+                                                (uint32_t)(j / kStages) & 1u, lim);
+                }
+                __syncwarp();
                 return;
             }
             const int a0 = c * g.ch;
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const float2 kNeg1 = make_float2(-1.0f, -1.0f), kHalf2 = make_float2(0.5f, 0.5f);
     for (int c = 0; c < nch; ++c) {
         const int s = c % kStages;
-        const bool ok = mbar_wait_bounded(full0 + 8u * s, (uint32_t)(c / kStages) & 1u);
+        const bool ok = mbar_wait_bounded(full0 + 8u * s, (uint32_t)(c / kStages) & 1u, lim);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) *reinterpret_cast<volatile int *>(g.status) = FBP_ERR_TIMEOUT;
             return;
@@ -355,6 +364,9 @@ void free_fdk(FdkPlan *f)
 }
 
 }  // namespace
+
+cudaError_t set_wait_hook_fdk(const WaitHook &h) { return write_wait_hook(h); }
+
 }  // namespace fbp
 
 using namespace fbp;

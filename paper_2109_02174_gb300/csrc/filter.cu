@@ -61,6 +61,16 @@ cudaError_t launch(const Plan &p, const float *sino, int ld, OutT *q, cudaStream
 
 size_t filter_direct_smem_bytes(int D) { return sizeof(float) * (size_t)(4 * D + 1); }
 
+cudaError_t prepare_filter_direct(const Plan &p)
+{
+    const int smem = (int)filter_direct_smem_bytes(p.D);
+    if (p.q_storage == FBP_F16)
+        return cudaFuncSetAttribute(filter_direct_kernel<__half>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(filter_direct_kernel<float>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_filter_direct(const Plan &p, const float *sino, int ld, void *q,
                                  cudaStream_t s)
 {

@@ -463,6 +463,16 @@ cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q,
     return launch_set<float, 1>(L, L.s[0].block_end, p.fft_len, s);
 }
 
+cudaError_t prepare_filter_fft(const Plan &p)
+{
+    const int smem = (int)filter_fft_smem_bytes(p.fft_len);
+    if (p.q_storage == FBP_F16)
+        return cudaFuncSetAttribute(filter_fft_kernel<__half, 1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(filter_fft_kernel<float, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_filter_fft_many(const Plan *const *plans, const float *const *sinos,
                                    const int *lds, void *const *qs, int n, cudaStream_t s)
 {

@@ -27,12 +27,17 @@
 // (correctly rounded) as soon as its MMAs complete, then hand back to the MMA
 // warp.  The lo parts are rounded to tf32 (to nearest) before they reach the
 // tensor core, so its truncation of them leaves no sign-correlated error.
-// Every wait is bounded; on a timeout the CTA records the status, releases its
-// tensor memory and exits.
+// Every wait is bounded (the run-time limit of WaitHook); on a timeout the CTA
+// records the status and every warp stops: the MMA warp then waits (bounded)
+// for the MMAs it committed, the TMA warp for the loads it issued, and the
+// CTA releases its tensor memory and exits with nothing in flight.  For
+// tests, the first CTA can withhold the loader warps' arrival on one stage,
+// which makes the MMA warp's wait on it run out.
 #include "fbp_internal.h"
 #include "filter_tc.cuh"
 #include "lambert.cuh"
 #include "ptx.cuh"
+#include "waithook.cuh"
 
 #include <cstring>
 
@@ -241,21 +246,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         *reinterpret_cast<volatile int *>(args.status) = FBP_ERR_TIMEOUT;
         *abort_flag = 1;
     };
+    const WaitHook hook = g_wait_hook;
+    const unsigned long long lim = wait_limit_ns(hook);
 
     if (warp == 0) {
         // -------------------------------------------------------- MMA issuer
         if (lane == 0) {
+            int committed = -1;  // last K chunk whose MMAs were committed
             for (int kc = 0; kc < args.nk && !*abort_flag; ++kc) {
                 const int s = kc % kStages;
                 const uint32_t ph = (uint32_t)(kc / kStages) & 1u;
-                if (!mbar_wait_bounded(bar_full_a + 8 * s, ph) ||
-                    !mbar_wait_bounded(bar_full_b + 8 * s, ph)) {
+                if (!mbar_wait_bounded(bar_full_a + 8 * s, ph, lim) ||
+                    !mbar_wait_bounded(bar_full_b + 8 * s, ph, lim)) {
                     fail();
                     break;
                 }
                 const int blk = kc % kAcc;
                 if (kc >= kAcc &&
-                    !mbar_wait_bounded(bar_acc_free + 8 * blk, (uint32_t)(kc / kAcc - 1) & 1u)) {
+                    !mbar_wait_bounded(bar_acc_free + 8 * blk, (uint32_t)(kc / kAcc - 1) & 1u,
+                                       lim)) {
                     fail();
                     break;
                 }
@@ -273,16 +282,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 mma_commit(bar_empty + 8 * s);     // stage s free once these MMAs have read it
                 mma_commit(bar_acc_full + 8 * blk);  // chunk kc's partial sums are ready
+                committed = kc;
             }
+            // stopped early: the MMAs already issued finish before the tensor
+            // memory they write is released (a commit tracks all earlier ones)
+            if (*abort_flag && committed >= 0)
+                (void)mbar_wait_bounded(bar_empty + 8 * (committed % kStages),
+                                        (uint32_t)(committed / kStages) & 1u, lim);
         }
         __syncwarp();
     } else if (warp == 1) {
         // -------------------------------------------------------- T tiles by TMA
         if (lane == 0) {
+            int issued = 0;  // K chunks whose T tiles were requested
             for (int kc = 0; kc < args.nk && !*abort_flag; ++kc) {
                 const int s = kc % kStages;
                 const uint32_t use = (uint32_t)(kc / kStages);
-                if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u)) {
+                if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u, lim)) {
                     fail();
                     break;
                 }
@@ -290,11 +306,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_arrive_expect_tx(bar_full_b + 8 * s, 2 * kTile);
                 tma_load_2d(st + 2 * kTile, &t_hi, kc * kBK, n0, bar_full_b + 8 * s);
                 tma_load_2d(st + 3 * kTile, &t_lo, kc * kBK, n0, bar_full_b + 8 * s);
+                issued = kc + 1;
             }
+            // stopped early: the last kStages requests (each its stage's latest
+            // phase) land before the CTA leaves
+            if (*abort_flag)
+                for (int j = (issued > kStages ? issued - kStages : 0); j < issued; ++j)
+                    (void)mbar_wait_bounded(bar_full_b + 8 * (j % kStages),
+                                            (uint32_t)(j / kStages) & 1u, lim);
         }
         __syncwarp();
     } else {
         // -------------------------------------------------------- A split, then epilogue
+        const int withhold =
+            withheld_stage(hook, kWithholdFilterTc, blockIdx.x == 0 && blockIdx.y == 0);
         const int cw = warp - 2;  // rows 16 cw .. 16 cw + 15 of the tile
         const int quarter = warp & 3;   // TMEM lanes 32 quarter .. +31 = tile rows
         const int half = (warp - 2) / 4;
@@ -307,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // Add chunk kc2's accumulator into the FP32 sums, then free it.
         auto drain = [&](int kc2) -> bool {
             const int blk = kc2 % kAcc;
-            if (!mbar_wait_bounded(bar_acc_full + 8 * blk, (uint32_t)(kc2 / kAcc) & 1u)) {
+            if (!mbar_wait_bounded(bar_acc_full + 8 * blk, (uint32_t)(kc2 / kAcc) & 1u, lim)) {
                 fail();
                 return false;
             }
@@ -340,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = false;
                 break;
             }
-            if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u)) {
+            if (use > 0 && !mbar_wait_bounded(bar_empty + 8 * s, (use - 1) & 1u, lim)) {
                 fail();
                 ok = false;
                 break;
@@ -364,7 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 *reinterpret_cast<uint32_t *>(a_lo + off) = lo;
             }
             fence_proxy_async_smem();  // generic-proxy stores -> tensor-core reads
-            mbar_arrive_cta(bar_full_a + 8 * s);
+            // (tests only: the first CTA may withhold one stage's arrival)
+            if (kc != withhold) mbar_arrive_cta(bar_full_a + 8 * s);
 #pragma unroll
             for (int i = 0; i < kRowsPerLoader; ++i) cur[i] = nxt[i];
             if (kc >= 1) ok = drain(kc - 1);  // the previous chunk's MMAs are (nearly) done
@@ -393,6 +419,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 }  // namespace
+
+cudaError_t set_wait_hook_filter_tc(const WaitHook &h) { return write_wait_hook(h); }
 
 size_t filter_tc_smem_bytes()
 {
@@ -433,6 +461,13 @@ cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, cons
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t prepare_filter_tc(const Plan &p)
+{
+    return cudaFuncSetAttribute(p.i0 > 0.0 ? filter_tc_kernel<true> : filter_tc_kernel<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)filter_tc_smem_bytes());
 }
 
 cudaError_t launch_filter_tc(const Plan &p, const float *sino, int ld, float *q, cudaStream_t s)

@@ -245,6 +245,21 @@ cudaError_t launch_filter_fft_f64(const Plan &p, const double *sino, int ld, dou
     return cudaGetLastError();
 }
 
+cudaError_t prepare_fp64(const Plan &p)
+{
+    cudaError_t e;
+    if (p.filter_path == FBP_PATH_FFT)
+        e = cudaFuncSetAttribute(filter_fft_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)filter_fft_f64_smem_bytes(p.fft_len));
+    else
+        e = cudaFuncSetAttribute(filter_direct_f64_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)filter_direct_f64_smem_bytes(p.D));
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, backproject_f64_kernel);
+    return e;
+}
+
 cudaError_t launch_backproject_f64(const Plan &p, const double *q, double *image, cudaStream_t s)
 {
     dim3 grid((p.n + 15) / 16, (p.n + 15) / 16);

@@ -11,12 +11,18 @@
 // Such callers still own the sinogram and the image; the only scratch, the
 // filtered sinogram, lives in a fixed array compiled into this library.
 //
-// The array below is a device symbol: every GPU that loads libfbp holds
-// kStaticScratchBytes of it until the process exits.  Host code must never
-// pass the symbol itself to a kernel (on the host it names a host-side shadow,
-// not device memory); its device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// The array below is a device symbol: every GPU that loads libfbp's module
+// holding it keeps kStaticScratchBytes of it until the process exits.  Host
+// code must never pass the symbol itself to a kernel (on the host it names a
+// host-side shadow, not device memory); its device address comes from
+// cudaGetSymbolAddress, called with the device current.  That call is the
+// set-up: fbp_plan makes it for its device after building the plan (CUDA loads
+// modules lazily, so this is also where the array becomes resident on that
+// device), and fbp_reconstruct_static only reads the address it left.  Every
+// plan refreshes the address, so a plan made after a cudaDeviceReset (which
+// invalidates earlier plans) never hands out a stale one.
 #include <mutex>
+#include <string>
 
 #include "fbp_internal.h"
 
@@ -31,8 +37,10 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
+std::string g_scratch_err[kMaxDevices];
 
-// Device address of the scratch array on the current device (set-up on first use).
+// The scratch array's device address on `device` (current), as the last plan
+// made on it found it.
 fbp_status static_scratch(int device, void **out)
 {
     if (device < 0 || device >= kMaxDevices) {
@@ -41,19 +49,34 @@ fbp_status static_scratch(int device, void **out)
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (g_scratch_ptr[device] == nullptr) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess || ptr == nullptr) {
-            set_error("fbp_reconstruct_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            return FBP_ERR_CUDA;
-        }
-        g_scratch_ptr[device] = ptr;
+        set_error("fbp_reconstruct_static: no scratch address on device %d (%s)", device,
+                  g_scratch_err[device].empty() ? "no plan was made on it"
+                                                : g_scratch_err[device].c_str());
+        return FBP_ERR_CUDA;
     }
     *out = g_scratch_ptr[device];
     return FBP_OK;
 }
 
 }  // namespace
+
+void static_scratch_setup(int device)
+{
+    if (device < 0 || device >= kMaxDevices) return;
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (e != cudaSuccess || ptr == nullptr) {
+        // fbp_reconstruct_static reports this; every other call is unaffected
+        g_scratch_ptr[device] = nullptr;
+        g_scratch_err[device] = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        (void)cudaGetLastError();
+        return;
+    }
+    g_scratch_ptr[device] = ptr;
+    g_scratch_err[device].clear();
+}
+
 }  // namespace fbp
 
 extern "C" fbp_status fbp_reconstruct_static(fbp_plan_t plan, const void *sino, int ld_sino,

@@ -8,8 +8,20 @@
 
 namespace fbp {
 
-// Limit of every device-side wait (ns of %globaltimer).
+// Default limit of every device-side wait (ns of %globaltimer).
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// Run-time settings of the bounded waits (fbp_set_wait_limit and the
+// test-only fbp_test_withhold_arrival).  Every translation unit with waiting
+// kernels holds one copy as a device variable (waithook.cuh), which its kernels
+// read when they start, so the settings also reach kernels of CUDA graphs
+// captured before they changed.
+enum : int { kWithholdNone = 0, kWithholdBackproject = 1, kWithholdFilterTc = 2 };
+struct WaitHook {
+    unsigned long long limit_ns;  // 0: kWaitLimitNs
+    int kind;                     // kWithhold*: kernel kind whose first CTA withholds ...
+    int stage;                    // ... the arrival of this stage (ring fill) of its pipeline
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -54,13 +66,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return done != 0;
 }
 
-// Wait for the phase with the given parity to complete; false after the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+// Wait for the phase with the given parity to complete; false once limit_ns
+// have passed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_timer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+        if (global_timer_ns() - t0 > limit_ns) return false;
     }
     return true;
 }

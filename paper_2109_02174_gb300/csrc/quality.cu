@@ -12,14 +12,22 @@
 //      differences (each difference of two floats formed exactly in FP64),
 //      max |reference|, min and max of the reference;
 //   2. consts: one thread turns the block results into L, C1, C2;
-//   3. ssim: one CTA per 32 x 32 block of window positions; the (32+10)^2
+//   3. ssim: one CTA per 16 x 16 block of window positions; the (16+10)^2
 //      patch of both images sits in shared memory; the Gaussian is separable
-//      (w[a][b] = g[a] g[b]), so a horizontal then a vertical pass give the
-//      local means of x, y, x^2, y^2 and xy in FP32; per window
-//      sigma_x^2 = E[x^2] - mu_x^2 and sigma_xy = E[xy] - mu_x mu_y; the
-//      CTA's sum of SSIM values in FP64;
+//      (w[a][b] = g[a] g[b]), so a horizontal then a vertical pass give, in
+//      FP64, the local means of x, y, x^2 + y^2, d = x - y and d^2 (products
+//      and the difference of two floats are exact in FP64).  Per window the
+//      SSIM is formed through its distance from 1, which needs no
+//      cancellation of large terms:
+//        1 - l  = (E[d])^2 / (mu_x^2 + mu_y^2 + C1)            (l: luminance)
+//        1 - cs = Var(d) / (sigma_x^2 + sigma_y^2 + C2)         (cs: the rest)
+//        1 - SSIM = (1 - l) + (1 - cs) - (1 - l)(1 - cs),
+//      with Var(d) = E[d^2] - (E[d])^2 = sigma_x^2 + sigma_y^2 - 2 sigma_xy
+//      (clamped at 0); so a pair of near-identical images keeps 1 - SSIM to
+//      the precision of the differences, and SSIM never exceeds 1.  The CTA's
+//      sum of (1 - SSIM) values in FP64;
 //   4. finish: one CTA sums the partial results in order and writes
-//      out[0] = PSNR (dB), out[1] = mean SSIM.
+//      out[0] = PSNR (dB), out[1] = 1 - mean(1 - SSIM).
 #include <cmath>
 #include <cstring>
 
@@ -30,13 +38,13 @@ namespace {
 
 constexpr int kWin = 11;           // SSIM window side
 constexpr int kHalo = kWin - 1;    // extra rows/columns a tile reads
-constexpr int kTile = 32;          // window positions per CTA side
+constexpr int kTile = 16;          // window positions per CTA side
 constexpr int kPatch = kTile + kHalo;
 constexpr int kStatBlocks = 256;   // CTAs of the stats pass
 constexpr int kThreads = 256;
 
 struct Gauss {
-    float g[kWin];  // normalised 1-D Gaussian, sigma 1.5
+    double g[kWin];  // normalised 1-D Gaussian, sigma 1.5
 };
 
 // Scratch layout (offsets in bytes, each part 256-byte aligned).
@@ -138,8 +146,9 @@ __global__ void __launch_bounds__(kThreads)
 {
     __shared__ float px[kPatch][kPatch + 1];
     __shared__ float py[kPatch][kPatch + 1];
-    // horizontal pass results: [map][patch row][tile column]
-    __shared__ float hz[5][kPatch][kTile + 1];
+    // horizontal pass results: [map][patch row][tile column], maps
+    // x, y, x^2 + y^2, d, d^2 (d = x - y)
+    __shared__ double hz[5][kPatch][kTile + 1];
     __shared__ double shd[kThreads];
     const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
     for (int t = threadIdx.x; t < kPatch * kPatch; t += kThreads) {
@@ -152,43 +161,46 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     for (int t = threadIdx.x; t < kPatch * kTile; t += kThreads) {
         const int r = t / kTile, c = t - r * kTile;
-        float sx = 0.0f, sy = 0.0f, sxx = 0.0f, syy = 0.0f, sxy = 0.0f;
+        double sx = 0.0, sy = 0.0, s2 = 0.0, sd = 0.0, sdd = 0.0;
 #pragma unroll
         for (int b = 0; b < kWin; ++b) {
-            const float a = px[r][c + b], v = py[r][c + b], w = G.g[b];
-            sx = fmaf(w, a, sx);
-            sy = fmaf(w, v, sy);
-            sxx = fmaf(w, a * a, sxx);
-            syy = fmaf(w, v * v, syy);
-            sxy = fmaf(w, a * v, sxy);
+            const double a = px[r][c + b], v = py[r][c + b], w = G.g[b];
+            const double d = a - v;  // exact
+            sx = fma(w, a, sx);
+            sy = fma(w, v, sy);
+            s2 = fma(w, fma(a, a, v * v), s2);
+            sd = fma(w, d, sd);
+            sdd = fma(w, d * d, sdd);
         }
         hz[0][r][c] = sx;
         hz[1][r][c] = sy;
-        hz[2][r][c] = sxx;
-        hz[3][r][c] = syy;
-        hz[4][r][c] = sxy;
+        hz[2][r][c] = s2;
+        hz[3][r][c] = sd;
+        hz[4][r][c] = sdd;
     }
     __syncthreads();
     const double *cst = reinterpret_cast<const double *>(scratch + L.consts);
-    const float c1 = (float)cst[1], c2 = (float)cst[2];
+    const double c1 = cst[1], c2 = cst[2];
     double acc = 0.0;
     for (int t = threadIdx.x; t < kTile * kTile; t += kThreads) {
         const int r = t / kTile, c = t - r * kTile;
         if (i0 + r + kWin > rows || j0 + c + kWin > cols) continue;  // window leaves the image
-        float mx = 0.0f, my = 0.0f, exx = 0.0f, eyy = 0.0f, exy = 0.0f;
+        double mx = 0.0, my = 0.0, e2 = 0.0, md = 0.0, edd = 0.0;
 #pragma unroll
         for (int a = 0; a < kWin; ++a) {
-            const float w = G.g[a];
-            mx = fmaf(w, hz[0][r + a][c], mx);
-            my = fmaf(w, hz[1][r + a][c], my);
-            exx = fmaf(w, hz[2][r + a][c], exx);
-            eyy = fmaf(w, hz[3][r + a][c], eyy);
-            exy = fmaf(w, hz[4][r + a][c], exy);
+            const double w = G.g[a];
+            mx = fma(w, hz[0][r + a][c], mx);
+            my = fma(w, hz[1][r + a][c], my);
+            e2 = fma(w, hz[2][r + a][c], e2);
+            md = fma(w, hz[3][r + a][c], md);
+            edd = fma(w, hz[4][r + a][c], edd);
         }
-        const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
-        const float num = (2.0f * mx * my + c1) * (2.0f * cxy + c2);
-        const float den = (mx * mx + my * my + c1) * (vx + vy + c2);
-        acc += (double)num / (double)den;
+        const double m2 = fma(mx, mx, my * my);
+        const double vsum = e2 - m2;                      // sigma_x^2 + sigma_y^2
+        const double vd = fmax(fma(-md, md, edd), 0.0);   // Var(x - y)
+        const double one_l = md * md / (m2 + c1);
+        const double one_cs = vd / (vsum + c2);
+        acc += one_l + one_cs - one_l * one_cs;           // 1 - SSIM of this window
     }
     acc = block_reduce(acc, shd, [](double u, double v) { return u + v; });
     if (threadIdx.x == 0)
@@ -218,7 +230,7 @@ __global__ void __launch_bounds__(kThreads)
         const double mse = se / ((double)rows * (double)cols);
         out[0] = mse > 0.0 ? 20.0 * log10((double)mx / sqrt(mse)) : (double)INFINITY;
         const double windows = (double)(rows - kHalo) * (double)(cols - kHalo);
-        out[1] = nt > 0 ? s / windows : (double)NAN;
+        out[1] = nt > 0 ? 1.0 - s / windows : (double)NAN;
     }
 }
 
@@ -266,7 +278,7 @@ fbp_status fbp_quality(const void *image, const void *reference, int rows, int c
         g[a] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
         gs += g[a];
     }
-    for (int a = 0; a < kWin; ++a) G.g[a] = (float)(g[a] / gs);
+    for (int a = 0; a < kWin; ++a) G.g[a] = g[a] / gs;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float *x = static_cast<const float *>(image);
     const float *y = static_cast<const float *>(reference);

@@ -273,6 +273,8 @@ void worker_main(fbp_server_s *s)
         }
         if (progressed) s->cv_done.notify_all();
         // 2. admit in arrival order while the arena has room
+        if (!s->pending.empty()) nvtxRangePushA("serving admission");
+        const bool admitting = !s->pending.empty();
         while (!s->pending.empty()) {
             Req *q = s->pending.front();
             if (q->state == ST_CANCELLED) {
@@ -296,6 +298,7 @@ void worker_main(fbp_server_s *s)
             s->ready.push_back(q);
             progressed = true;
         }
+        if (admitting) nvtxRangePop();
         // 3. launch waves on free streams
         while (!s->ready.empty()) {
             int si = -1;
@@ -312,7 +315,12 @@ void worker_main(fbp_server_s *s)
             }
             s->stream_busy[(size_t)si] = true;
             ++s->waves;
-            if (!launch_wave(s, w, si)) {
+            bool launched;
+            {
+                NvtxRange range("serving wave launch");
+                launched = launch_wave(s, w, si);
+            }
+            if (!launched) {
                 s->last_error = cudaGetErrorString(cudaGetLastError());
                 // work already enqueued may still touch the wave's memory
                 cudaStreamSynchronize(s->streams[(size_t)si]);

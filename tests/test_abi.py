@@ -71,3 +71,15 @@ def test_autotune_argument_errors_need_no_gpu(lib):
     t = fbp.fbp_tuning()
     assert lib.fbp_autotune(64, 90, 92, 1.0, 0, None, 0, ctypes.byref(t)) == fbp.FBP_ERR_INVALID_ARG
     assert lib.fbp_autotune(64, 90, 92, 1.0, 0, None, 4, None) == fbp.FBP_ERR_INVALID_ARG
+
+
+def test_wait_settings_argument_errors_need_no_gpu(lib):
+    """The wait-limit and test-hook calls check their arguments before they
+    look for a device."""
+    import paper_2109_02174_gb300 as fbp
+    for bad in (-1.0, float("nan"), float("inf"), 1e-9, 1e5):
+        assert lib.fbp_set_wait_limit(bad) == fbp.FBP_ERR_INVALID_ARG, bad
+    assert "fbp_set_wait_limit" in fbp.fbp_last_error()
+    assert lib.fbp_test_withhold_arrival(9, 0) == fbp.FBP_ERR_INVALID_ARG
+    assert lib.fbp_test_withhold_arrival(fbp.FBP_TEST_WITHHOLD_FILTER_TC, -1) == \
+        fbp.FBP_ERR_INVALID_ARG

@@ -200,8 +200,10 @@ def test_same_plan_slices_pair_up_bitwise(fbp, q_storage):
 def test_batched_uneven_workload_64(fbp):
     """The batched configuration: 64 uneven slices (n in {256,384,512,768},
     A in {180,360,720,1440}) in one graph.  Every slice is bit-identical to its
-    alone result; four slices, the largest among them, are checked against the
-    oracle at sampled pixels."""
+    alone result, and every pixel of every slice is within the FP32 bars of the
+    oracle's image."""
+    import os
+
     import torch
     specs = synthetic.cfg_batch()
     plans = [fbp.Plan(s.n_pix, s.n_angles, s.n_det) for s in specs]
@@ -213,17 +215,14 @@ def test_batched_uneven_workload_64(fbp):
     imgs = [im.cpu().numpy() for im in batch.images]
     for plan, sino, img in zip(plans, sinos, imgs):
         assert np.array_equal(img, _alone(fbp, plan, sino))
-    big = max(range(64), key=lambda i: specs[i].updates)
-    for i in sorted({big, 0, 17, 42}):
-        s = specs[i]
+    for i, s in enumerate(specs):
         th = synthetic.default_angles(s.n_angles)
-        Q = oracle.filter_rows(sinos[i].double().cpu().numpy(), s.filter, 1.0, nthreads=NTHREADS)
-        rng = np.random.default_rng(i)
-        rows = rng.integers(0, s.n_pix, 400)
-        cols = rng.integers(0, s.n_pix, 400)
-        ref = oracle.backproject_pixels(Q, th, 1.0, s.n_pix, rows, cols)
-        err = np.abs(imgs[i][rows, cols] - ref) / np.abs(ref).max()
-        assert err.max() <= MAX_REL and np.sqrt(np.mean(err ** 2)) <= RMSE_REL
+        ref = oracle.fbp(sinos[i].double().cpu().numpy(), th, s.tau, s.filter, s.n_pix,
+                         nthreads=os.cpu_count() or 1)
+        scale = np.abs(ref).max()
+        err = imgs[i].astype(np.float64) - ref
+        assert np.abs(err).max() <= MAX_REL * scale, (i, np.abs(err).max() / scale)
+        assert np.sqrt(np.mean(err ** 2)) <= RMSE_REL * scale, i
 
 
 def test_batch_argument_errors(fbp):

@@ -79,3 +79,15 @@ def test_fdk_deterministic_and_rejects_bad_geometry(fbp):
     with pytest.raises(fbp.FbpError) as e:
         fbp.FdkPlan(40, 16, 40, 10.0, 32, 32, 16)  # the volume reaches the source circle
     assert e.value.status == fbp.FBP_ERR_INVALID_ARG
+
+
+def test_fdk_bench_geometry_every_voxel(fbp):
+    """The reconstruction bench.py times: 256^3 voxels from 360 projections of
+    448 x 320 bins over a full turn, source radius 1024 (its largest windows
+    and stage ring), seeded normal projections, Ram-Lak.  Every voxel against
+    the oracle's volume."""
+    A, nv, nu = 360, 320, 448
+    P = np.random.default_rng(26).standard_normal((A, nv, nu)).astype(np.float32)
+    beta = synthetic.cone_beta(A)
+    got, ref, _ = _run(fbp, P, beta, 1024.0, 1.0, 1.0, 0, 256, 256, 256, give_beta=False)
+    _assert_bars(got, ref)

@@ -235,26 +235,14 @@ def test_float_slice_512_noisy(fbp, path):
     _check_slice(fbp, synthetic.cfg_float_double(), filter_path=PATHS[path])
 
 
-def test_large_slice_2048_sampled(fbp):
-    """2048x2048, 2048 angles, 2899 bins: GPU image checked at sampled pixels
-    against the oracle's per-pixel Eq. 2 over the oracle's own filtered rows."""
-    spec = synthetic.cfg_large()
-    th = synthetic.default_angles(spec.n_angles)
-    sino32 = synthetic.sinogram(spec, th).astype(np.float32)
+def test_large_slice_2048_every_pixel(fbp, large_reference):
+    """2048x2048, 2048 angles, 2899 bins (40 ellipses, seed 4), default plan:
+    every pixel of the GPU image against the oracle's whole image."""
+    spec, th, sino32, ref = large_reference
     plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det, filter=spec.filter)
     got = _np(plan.reconstruct(_t(sino32)))
-    Q = oracle.filter_rows(sino32.astype(np.float64), spec.filter, 1.0, nthreads=NTHREADS)
-    rng = np.random.default_rng(2048)
-    g = np.arange(0, spec.n_pix, 64)
-    gr, gc = np.meshgrid(g, g, indexing="ij")
-    rows = np.concatenate([rng.integers(0, spec.n_pix, 300), gr.ravel(), [0, 2047, 1024, 0, 2047]])
-    cols = np.concatenate([rng.integers(0, spec.n_pix, 300), gc.ravel(), [0, 2047, 1023, 2047, 0]])
-    ref = oracle.backproject_pixels(Q, th, 1.0, spec.n_pix, rows, cols)
-    # max over the sampled oracle values: a lower bound of max|f|, so the bar is stricter
-    scale = float(np.abs(ref).max())
-    err = np.abs(got[rows, cols] - ref) / scale
-    assert err.max() <= MAX_REL and np.sqrt(np.mean(err ** 2)) <= RMSE_REL, \
-        f"max {err.max():.3e} rms {np.sqrt(np.mean(err ** 2)):.3e}"
+    plan.device_status()
+    assert_parity(got, ref)
 
 
 # ---------------------------------------------------------------- precision variants

@@ -3,10 +3,17 @@
 It serves callers that cannot allocate device memory when they reconstruct
 (a fixed-deadline acquisition loop that cannot absorb cudaMalloc's device-wide
 synchronisation, or a host whose device memory belongs to another allocator).
-Its scratch is a static device array inside libfbp.  Here it is called through
-the C ABI twice in a row, on two different sinograms, and each result must
-match fbp_reconstruct (with a caller workspace) within the parity tolerance
-used by the other GPU tests.  This file is collected last on purpose.
+Its scratch is a static device array inside libfbp, whose address fbp_plan
+looks up.  Here it is called through the C ABI:
+  - first on an all-NaN sinogram, which leaves NaN throughout the shared
+    array, so a later call that read anything it did not write would show it;
+  - then twice in a row on two different sinograms, each result equal bit for
+    bit to fbp_reconstruct with a caller workspace (same kernels, same bits)
+    and within the parity tolerance of the other GPU tests;
+  - with the device's free memory measured before the first of these calls
+    and after the last: unchanged.
+This file is collected last on purpose; it passes alone in a fresh process and
+after the other tests.
 """
 import numpy as np
 import pytest
@@ -44,21 +51,41 @@ def test_static_scratch_matches_workspace_path_twice(fbp):
     assert plan.workspace_bytes <= 16 * 1024 * 1024
     stream = torch.cuda.current_stream()
     sp = int(stream.cuda_stream)
+    # every buffer and every reference result first: nothing below allocates
+    poison = torch.full((spec.n_angles, spec.n_det), float("nan"), device="cuda")
+    sinos, refs, outs = [], [], []
     for seed in (1, 2):
         s = synthetic.SliceSpec(spec.n_pix, spec.n_angles, spec.n_det, 10, seed=seed)
         sino = torch.from_numpy(synthetic.sinogram(s).astype(np.float32)).cuda()
-        ref = plan.reconstruct(sino)
-        out = torch.full_like(ref, float("nan"))
+        sinos.append(sino)
+        refs.append(plan.reconstruct(sino))
+        outs.append(torch.full_like(refs[-1], float("nan")))
+    junk = torch.empty_like(refs[0])
+    torch.cuda.synchronize()
+    plan.device_status()
+    free_before = torch.cuda.mem_get_info()[0]
+
+    fbp.fbp_reconstruct_static(plan.handle, poison.data_ptr(), poison.stride(0),
+                               junk.data_ptr(), sp)
+    for sino, out in zip(sinos, outs):
         fbp.fbp_reconstruct_static(plan.handle, sino.data_ptr(), sino.stride(0),
                                    out.data_ptr(), sp)
-        torch.cuda.synchronize()
-        plan.device_status()
-        _close(out.double().cpu().numpy(), ref.double().cpu().numpy())
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    plan.device_status()
+
+    assert torch.isnan(junk).all()  # the poison went through the shared array
+    for ref, out in zip(refs, outs):
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert np.array_equal(got, ref.cpu().numpy())
+        _close(got.astype(np.float64), ref.double().cpu().numpy())
+    assert free_after == free_before, f"device free memory moved by {free_before - free_after} B"
 
 
 def test_static_scratch_rejects_plans_beyond_its_capacity(fbp):
     import torch
-    spec = synthetic.cfg_large()  # 2048 angles x 2904-float rows: 23.8 MB > 16 MiB
+    spec = synthetic.cfg_large()  # 2048 angles x 5808-float rows: 47.6 MB > 16 MiB
     plan = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det)
     assert plan.workspace_bytes > 16 * 1024 * 1024
     sino = torch.zeros((spec.n_angles, spec.n_det), device="cuda")
