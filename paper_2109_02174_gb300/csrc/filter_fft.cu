@@ -30,6 +30,7 @@
 #include "lambert.cuh"
 #include "pairs.cuh"
 
+#include <cstring>
 #include <vector>
 
 namespace fbp {
@@ -86,6 +87,25 @@ template <bool INV>
 __device__ __forceinline__ Tw tw_load(const float4 *__restrict__ tw, int t)
 {
     const float4 v = __ldg(&tw[t]);
+    const float2 s = make_float2(v.z, v.w);
+    const float2 n = pneg(s);
+    Tw w;
+    w.r = make_float2(v.x, v.y);
+    w.s = INV ? n : s;
+    w.n = INV ? s : n;
+    return w;
+}
+
+// tw_load through a volatile load: the last pass's twiddles stay after the
+// preceding exchange (hoisted above it, fourteen of them would be live across
+// it and spill registers).
+template <bool INV>
+__device__ __forceinline__ Tw tw_load_late(const float4 *__restrict__ tw, int t)
+{
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(tw + t));
     const float2 s = make_float2(v.z, v.w);
     const float2 n = pneg(s);
     Tw w;
@@ -193,6 +213,86 @@ __device__ __forceinline__ void dft16(C2 (&v)[16])
     for (int m = 0; m < 16; ++m) v[m] = x[m];
 }
 
+// 4-point DFT of (a0, a1, 0, 0): the first stage of a transform whose upper
+// half of inputs is zero padding (the same values dft4 gives for those inputs).
+template <bool INV>
+__device__ __forceinline__ void dft4_z23(C2 &a0, C2 &a1, C2 &a2, C2 &a3)
+{
+    const C2 b = a0, d = a1;
+    a0 = cadd(b, d);
+    a2 = csub(b, d);
+    if (INV) {
+        a1 = {psub(b.re, d.im), padd(b.im, d.re)};
+        a3 = {padd(b.re, d.im), psub(b.im, d.re)};
+    } else {
+        a1 = {padd(b.re, d.im), psub(b.im, d.re)};
+        a3 = {psub(b.re, d.im), padd(b.im, d.re)};
+    }
+}
+
+// 4-point DFT computing outputs 0 and 1 only (2 and 3 are not needed).
+template <bool INV>
+__device__ __forceinline__ void dft4_out01(C2 &a0, C2 &a1, const C2 &a2, const C2 &a3)
+{
+    const C2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), d = csub(a1, a3);
+    a0 = cadd(b0, b2);
+    a1 = INV ? C2{psub(b1.re, d.im), padd(b1.im, d.re)} : C2{padd(b1.re, d.im), psub(b1.im, d.re)};
+}
+
+// 16-point DFT (as dft16) with two prunings: ZHI, inputs 8..15 are zero;
+// OLO, only outputs 0..7 are needed (8..15 are left unspecified).
+template <bool INV, bool ZHI, bool OLO>
+__device__ __forceinline__ void dft16p(C2 (&v)[16])
+{
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) {
+        if constexpr (ZHI)
+            dft4_z23<INV>(v[q1], v[q1 + 4], v[q1 + 8], v[q1 + 12]);
+        else
+            dft4<INV>(v[q1], v[q1 + 4], v[q1 + 8], v[q1 + 12]);
+    }
+    v[5] = twiddle16<INV, 1>(v[5]);
+    v[9] = twiddle16<INV, 2>(v[9]);
+    v[13] = twiddle16<INV, 3>(v[13]);
+    v[6] = twiddle16<INV, 2>(v[6]);
+    v[10] = twiddle16<INV, 4>(v[10]);
+    v[14] = twiddle16<INV, 6>(v[14]);
+    v[7] = twiddle16<INV, 3>(v[7]);
+    v[11] = twiddle16<INV, 6>(v[11]);
+    v[15] = twiddle16<INV, 9>(v[15]);
+#pragma unroll
+    for (int m2 = 0; m2 < 4; ++m2) {
+        if constexpr (OLO)
+            dft4_out01<INV>(v[4 * m2], v[4 * m2 + 1], v[4 * m2 + 2], v[4 * m2 + 3]);
+        else
+            dft4<INV>(v[4 * m2], v[4 * m2 + 1], v[4 * m2 + 2], v[4 * m2 + 3]);
+    }
+    // X[m2 + 4 m1] sits in v[m1 + 4 m2]: transpose
+    C2 x[16];
+#pragma unroll
+    for (int m2 = 0; m2 < 4; ++m2)
+#pragma unroll
+        for (int m1 = 0; m1 < (OLO ? 2 : 4); ++m1) x[m2 + 4 * m1] = v[m1 + 4 * m2];
+#pragma unroll
+    for (int m = 0; m < (OLO ? 8 : 16); ++m) v[m] = x[m];
+}
+
+// 8-point DFT computing outputs 0..3 only.
+template <bool INV>
+__device__ __forceinline__ void dft8_lo4(C2 (&a)[8])
+{
+    dft4<INV>(a[0], a[2], a[4], a[6]);
+    dft4<INV>(a[1], a[3], a[5], a[7]);
+    a[3] = twiddle16<INV, 2>(a[3]);
+    a[5] = twiddle16<INV, 4>(a[5]);
+    a[7] = twiddle16<INV, 6>(a[7]);
+    C2 x[4];
+#pragma unroll
+    for (int m2 = 0; m2 < 4; ++m2) x[m2] = cadd(a[2 * m2], a[2 * m2 + 1]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) a[m] = x[m];
+}
+
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ void put(float4 *buf, int i, const C2 &a)
@@ -205,88 +305,141 @@ __device__ __forceinline__ C2 get(const float4 *buf, int i)
     return {make_float2(f.x, f.y), make_float2(f.z, f.w)};
 }
 
-// Full N-point transform of the elements the block holds (thread t: positions
-// t + q N/16 in v[q]); on return v[q] holds output position t + q N/16.
-template <bool INV>
-__device__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 *__restrict__ tw, int N,
-                         int log2n)
+// Full N-point transform (N = 2^L, T = N/16 threads) of the elements the
+// block holds (thread t: positions t + q T in v[q]); on return v[q] holds
+// output position t + q T.  Compile-time N: every shared-memory and table
+// index below is a per-thread base plus a constant.  Prunings (values equal
+// to the unpruned transform's): FIRST_HALF_ZERO, inputs q >= 8 are zero (a
+// row zero-padded to N >= 2 n_det - 1 has n_det <= N/2); LAST_LO8, only
+// outputs q < 8 are needed (the bins 0..n_det-1 of the inverse).
+template <bool INV, int L, bool FIRST_HALF_ZERO, bool LAST_LO8>
+__device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 *__restrict__ tw)
 {
+    constexpr int N = 1 << L;
+    constexpr int T = N >> 4;
+    constexpr int NP = L >> 2;   // radix-16 passes
+    constexpr int REM = L & 3;   // bits of the last pass (radix 2^REM), 0: none
     const int t = threadIdx.x;
-    const int T = N >> 4;
-    const int n16 = log2n >> 2;
-    const int rem = log2n & 3;
-    int ns = 1, log2ns = 0;
-    for (int p = 0; p < n16; ++p) {
-        const bool last = rem == 0 && p == n16 - 1;
-        const int k = t & (ns - 1);
-        if (ns > 1) {
-            const int i1 = k << (log2n - 4 - log2ns);  // k N / (16 ns)
-            const Tw w1 = tw_load<INV>(tw, i1), w2 = tw_load<INV>(tw, 2 * i1);
-            const Tw w4 = tw_load<INV>(tw, 4 * i1), w8 = tw_load<INV>(tw, 8 * i1);
-            const Tw w3 = tmul(w1, w2);
-            v[1] = cmul(v[1], w1);
-            v[2] = cmul(v[2], w2);
-            v[3] = cmul(v[3], w3);
-            v[4] = cmul(v[4], w4);
-            v[5] = cmul(v[5], tmul(w4, w1));
-            v[6] = cmul(v[6], tmul(w4, w2));
-            v[7] = cmul(v[7], tmul(w4, w3));
-            v[8] = cmul(v[8], w8);
-            v[9] = cmul(v[9], tmul(w8, w1));
-            v[10] = cmul(v[10], tmul(w8, w2));
-            v[11] = cmul(v[11], tmul(w8, w3));
-            const Tw w12 = tmul(w8, w4);
-            v[12] = cmul(v[12], w12);
-            v[13] = cmul(v[13], tmul(w12, w1));
-            v[14] = cmul(v[14], tmul(w12, w2));
-            v[15] = cmul(v[15], tmul(w12, w3));
-        }
-        dft16<INV>(v);
-        if (!last) {
-            const int o = ((t - k) << 4) + k;
+    // the exchange after a radix-16 pass: write positions o + m ns from wb with
+    // stride ws (padded), read t + q T
+    auto exchange = [&](int wb, int ws) {
 #pragma unroll
-            for (int m = 0; m < 16; ++m) put(buf, o + m * ns, v[m]);
-            __syncthreads();
+        for (int m = 0; m < 16; ++m) {
+            const C2 &a = v[m];
+            buf[wb + m * ws] = make_float4(a.re.x, a.re.y, a.im.x, a.im.y);
+        }
+        __syncthreads();
+        if constexpr (T >= 16) {
+            const int rb = t + (t >> 4);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float4 f = buf[rb + q * (T + T / 16)];
+                v[q] = {make_float2(f.x, f.y), make_float2(f.z, f.w)};
+            }
+        } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[q] = get(buf, t + q * T);
-            __syncthreads();
         }
-        ns <<= 4;
-        log2ns += 4;
+        __syncthreads();
+    };
+    // pass 0 (ns = 1): no twiddles; outputs o + m, o = 16 t: padded 17 t + m
+    constexpr bool LAST0 = REM == 0 && NP == 1;
+    if constexpr (FIRST_HALF_ZERO && LAST0 && LAST_LO8) dft16p<INV, true, true>(v);
+    else if constexpr (FIRST_HALF_ZERO) dft16p<INV, true, false>(v);
+    else if constexpr (LAST0 && LAST_LO8) dft16p<INV, false, true>(v);
+    else dft16<INV>(v);
+    if constexpr (!LAST0) exchange(17 * t, 1);
+    // passes 1 .. NP-1 (ns = 16^p), kept as a loop whose trip count the
+    // compiler cannot see: straight-line (one middle pass, N = 2^9 .. 2^11), its
+    // schedule overlaps the passes and spills registers
+    int np = NP;
+    asm volatile("" : "+r"(np));
+#pragma unroll 1
+    for (int p = 1; p < np; ++p) {
+        const int log2ns = 4 * p;
+        const int ns = 1 << log2ns;
+        const bool last = REM == 0 && p == NP - 1;
+        const int k = t & (ns - 1);
+        const int i1 = k << (L - 4 - log2ns);  // k N / (16 ns)
+        const Tw w1 = tw_load<INV>(tw, i1), w2 = tw_load<INV>(tw, 2 * i1);
+        const Tw w4 = tw_load<INV>(tw, 4 * i1), w8 = tw_load<INV>(tw, 8 * i1);
+        const Tw w3 = tmul(w1, w2);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], tmul(w4, w1));
+        v[6] = cmul(v[6], tmul(w4, w2));
+        v[7] = cmul(v[7], tmul(w4, w3));
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], tmul(w8, w1));
+        v[10] = cmul(v[10], tmul(w8, w2));
+        v[11] = cmul(v[11], tmul(w8, w3));
+        const Tw w12 = tmul(w8, w4);
+        v[12] = cmul(v[12], w12);
+        v[13] = cmul(v[13], tmul(w12, w1));
+        v[14] = cmul(v[14], tmul(w12, w2));
+        v[15] = cmul(v[15], tmul(w12, w3));
+        if (LAST_LO8 && last) {
+            dft16p<INV, false, true>(v);
+        } else {
+            dft16<INV>(v);
+        }
+        if (!last) {
+            // outputs o + m ns, o = 16 (t - k) + k; padded pad16(o) + m (ns + ns/16)
+            const int o = ((t - k) << 4) + k;
+            exchange(pad16(o), ns + (ns >> 4));
+        }
     }
-    if (rem == 0) return;
-    // last pass, radix R = 2^rem, ns = N / R: butterfly j = t + m T (m < 16/R)
-    // takes positions j + s N/R = t + (m + s 16/R) T, twiddles exp(-+ 2 pi i s j / N)
-    if (rem == 3) {
+    if constexpr (REM == 0) return;
+    // last pass, radix R = 2^REM, ns = N / R: butterfly j = t + m T (m < 16/R)
+    // takes positions j + s N/R = t + (m + s 16/R) T, twiddles exp(-+ 2 pi i s j / N);
+    // with LAST_LO8 only the outputs at q = m + s 16/R < 8 are formed
+    if constexpr (REM == 3) {
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             const int j = t + m * T;
             C2 a[8];
 #pragma unroll
-            for (int s = 0; s < 8; ++s) a[s] = s ? cmul(v[m + 2 * s], tw_load<INV>(tw, s * j)) : v[m];
-            dft8<INV>(a);
+            for (int s = 0; s < 8; ++s) a[s] = s ? cmul(v[m + 2 * s], tw_load_late<INV>(tw, s * j)) : v[m];
+            if constexpr (LAST_LO8) {
+                dft8_lo4<INV>(a);
 #pragma unroll
-            for (int s = 0; s < 8; ++s) v[m + 2 * s] = a[s];
+                for (int s = 0; s < 4; ++s) v[m + 2 * s] = a[s];
+            } else {
+                dft8<INV>(a);
+#pragma unroll
+                for (int s = 0; s < 8; ++s) v[m + 2 * s] = a[s];
+            }
         }
-    } else if (rem == 2) {
+    } else if constexpr (REM == 2) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int j = t + m * T;
-            C2 a1 = cmul(v[m + 4], tw_load<INV>(tw, j));
-            C2 a2 = cmul(v[m + 8], tw_load<INV>(tw, 2 * j));
-            C2 a3 = cmul(v[m + 12], tw_load<INV>(tw, 3 * j));
-            dft4<INV>(v[m], a1, a2, a3);
-            v[m + 4] = a1;
-            v[m + 8] = a2;
-            v[m + 12] = a3;
+            C2 a1 = cmul(v[m + 4], tw_load_late<INV>(tw, j));
+            C2 a2 = cmul(v[m + 8], tw_load_late<INV>(tw, 2 * j));
+            C2 a3 = cmul(v[m + 12], tw_load_late<INV>(tw, 3 * j));
+            if constexpr (LAST_LO8) {
+                dft4_out01<INV>(v[m], a1, a2, a3);
+                v[m + 4] = a1;
+            } else {
+                dft4<INV>(v[m], a1, a2, a3);
+                v[m + 4] = a1;
+                v[m + 8] = a2;
+                v[m + 12] = a3;
+            }
         }
     } else {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int j = t + m * T;
-            C2 a1 = cmul(v[m + 8], tw_load<INV>(tw, j));
-            dft2<INV>(v[m], a1);
-            v[m + 8] = a1;
+            C2 a1 = cmul(v[m + 8], tw_load_late<INV>(tw, j));
+            if constexpr (LAST_LO8) {
+                v[m] = cadd(v[m], a1);
+            } else {
+                dft2<INV>(v[m], a1);
+                v[m + 8] = a1;
+            }
         }
     }
 }
@@ -318,18 +471,27 @@ struct FftLaunch {
     int log2n;
 };
 
-template <typename OutT, int MAXS>
-__global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __grid_constant__ FftLaunch<MAXS> L)
+// Blocks per SM the register budget is sized for: 128 registers a thread.
+constexpr int fft_min_blocks(int L)
 {
+    return ((1 << L) / 16) >= 32 ? 512 / ((1 << L) / 16) : 16;
+}
+
+template <typename OutT, int MAXS, int L>
+__global__ void __launch_bounds__((1 << L) / 16, fft_min_blocks(L))
+    filter_fft_kernel(const __grid_constant__ FftLaunch<MAXS> P)
+{
+    constexpr int N = 1 << L;
+    constexpr int T = N / 16;
     extern __shared__ float4 buf[];
-    int lo = 0, hi = L.n - 1;
+    int lo = 0, hi = P.n - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if ((int)blockIdx.x < L.s[mid].block_end) hi = mid; else lo = mid + 1;
+        if ((int)blockIdx.x < P.s[mid].block_end) hi = mid; else lo = mid + 1;
     }
-    const FftSlice &S = L.s[lo];
-    const int blk = (int)blockIdx.x - (lo > 0 ? L.s[lo - 1].block_end : 0);
-    const int N = L.N, D = S.D, T = N >> 4, t = threadIdx.x;
+    const FftSlice &S = P.s[lo];
+    const int blk = (int)blockIdx.x - (lo > 0 ? P.s[lo - 1].block_end : 0);
+    const int D = S.D, t = threadIdx.x;
     const int i0 = 4 * blk;
     const int rows = min(4, S.A - i0);  // 1..4 rows in this block
     // rows i0, i0+1 -> transform 0 (re, im); rows i0+2, i0+3 -> transform 1;
@@ -338,13 +500,14 @@ __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __gri
     const float *p1 = p0 + (rows > 1 ? S.ld : 0);
     const float *p2 = p0 + (rows > 2 ? 2 * (size_t)S.ld : 0);
     const float *p3 = p0 + (rows > 3 ? 3 * (size_t)S.ld : 0);
+    // n_det <= N/2: positions t + q T with q >= 8 are zero padding
     C2 v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const int j = t + q * T;
         v[q].re = make_float2(0.0f, 0.0f);
         v[q].im = make_float2(0.0f, 0.0f);
-        if (j < D) {
+        if (q < 8 && j < D) {
             v[q].re.x = p0[j];
             if (rows > 1) v[q].im.x = p1[j];
             if (rows > 2) v[q].re.y = p2[j];
@@ -354,7 +517,7 @@ __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __gri
     if (S.i0 > 0.0f) {
         // intensities: convert after all loads are in flight (the padding stays zero)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < 8; ++q) {
             if (t + q * T < D) {
                 v[q].re.x = line_integral(v[q].re.x, S.i0, S.ln_i0);
                 if (rows > 1) v[q].im.x = line_integral(v[q].im.x, S.i0, S.ln_i0);
@@ -371,7 +534,7 @@ __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __gri
         const float *w2 = S.wt + (size_t)((i0 + 2) % S.wt_rows) * D;
         const float *w3 = S.wt + (size_t)((i0 + 3) % S.wt_rows) * D;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < 8; ++q) {
             const int j = t + q * T;
             if (j < D) {
                 v[q].re.x *= __ldg(&w0[j]);
@@ -381,32 +544,39 @@ __global__ void __launch_bounds__(kMaxFftLen / 16) filter_fft_kernel(const __gri
             }
         }
     }
-    fft_regs<false>(v, buf, S.tw, N, L.log2n);
+    fft_regs<false, L, true, false>(v, buf, S.tw);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const float2 hv = __ldg(&S.h[t + q * T]);
         v[q].re = pmul(v[q].re, hv);
         v[q].im = pmul(v[q].im, hv);
     }
-    fft_regs<true>(v, buf, S.tw, N, L.log2n);
-    // every thread is past its last read of buf (the final pass of the inverse
-    // reads none; the one before ends with a barrier)
+    fft_regs<true, L, false, true>(v, buf, S.tw);
+    // v[q], q < 8, holds Q of the four rows at bin t + q T (bins past n_det are
+    // not zero: they are cleared below).  Every thread is past its last read of
+    // buf (the final pass of the inverse reads none; the one before ends with
+    // a barrier): publish the values so each thread can read its left
+    // neighbour's.  Layout (row 0, row 2, row 1, row 3).
 #pragma unroll
-    for (int q = 0; q < 16; ++q) put(buf, t + q * T, v[q]);
+    for (int q = 0; q < 8; ++q) put(buf, t + q * T, v[q]);
     __syncthreads();
-    // buf[k] holds Q of the four rows at bin k (k < n_det): (row 0, row 2,
-    // row 1, row 3); write (mid, slope) pairs.
+    // the pair at p = t + q T is (Q[p-1], Q[p]) -> (mid, slope), Q zero outside
+    // [0, n_det); p runs to pitch/2 - 1 <= n_det + 3 (<= N/2 + 3)
     OutT *r0 = static_cast<OutT *>(S.q) + (size_t)i0 * S.pitch;
-    for (int p = t; p < S.pitch / 2; p += T) {
-        float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a;
-        if (p <= D) {
-            if (p >= 1) a = buf[pad16(p - 1)];
-            if (p < D) b = buf[pad16(p)];
+    const int P2 = S.pitch / 2;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        if (q * T >= P2) break;
+        const int p = t + q * T;
+        if (p < P2) {
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a;
+            if (q < 8 && p < D) b = make_float4(v[q].re.x, v[q].re.y, v[q].im.x, v[q].im.y);
+            if (p >= 1 && p - 1 < D) a = buf[pad16(p - 1)];
+            store_pair(r0, p, a.x, b.x);
+            if (rows > 1) store_pair(r0 + S.pitch, p, a.z, b.z);
+            if (rows > 2) store_pair(r0 + 2 * (size_t)S.pitch, p, a.y, b.y);
+            if (rows > 3) store_pair(r0 + 3 * (size_t)S.pitch, p, a.w, b.w);
         }
-        store_pair(r0, p, a.x, b.x);
-        if (rows > 1) store_pair(r0 + S.pitch, p, a.z, b.z);
-        if (rows > 2) store_pair(r0 + 2 * (size_t)S.pitch, p, a.y, b.y);
-        if (rows > 3) store_pair(r0 + 3 * (size_t)S.pitch, p, a.w, b.w);
     }
 }
 
@@ -417,17 +587,36 @@ int log2_of(int N)
     return l;
 }
 
-template <typename OutT, int MAXS>
-cudaError_t launch_set(FftLaunch<MAXS> &L, int total, int N, cudaStream_t s)
+template <typename OutT, int MAXS, int L>
+cudaError_t launch_one_len(const FftLaunch<MAXS> &P, int total, cudaStream_t s, bool prepare)
 {
-    L.N = N;
-    L.log2n = log2_of(N);
-    const size_t smem = filter_fft_smem_bytes(N);
-    cudaError_t e = cudaFuncSetAttribute(filter_fft_kernel<OutT, MAXS>,
+    const size_t smem = filter_fft_smem_bytes(1 << L);
+    cudaError_t e = cudaFuncSetAttribute(filter_fft_kernel<OutT, MAXS, L>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    filter_fft_kernel<OutT, MAXS><<<total, N / 16, smem, s>>>(L);
+    if (e != cudaSuccess || prepare) return e;
+    filter_fft_kernel<OutT, MAXS, L><<<total, (1 << L) / 16, smem, s>>>(P);
     return cudaGetLastError();
+}
+
+// N = 16 .. 8192 (the plan keeps N within kMaxFftLen)
+template <typename OutT, int MAXS>
+cudaError_t launch_set(FftLaunch<MAXS> &P, int total, int N, cudaStream_t s, bool prepare = false)
+{
+    P.N = N;
+    P.log2n = log2_of(N);
+    switch (P.log2n) {
+    case 4: return launch_one_len<OutT, MAXS, 4>(P, total, s, prepare);
+    case 5: return launch_one_len<OutT, MAXS, 5>(P, total, s, prepare);
+    case 6: return launch_one_len<OutT, MAXS, 6>(P, total, s, prepare);
+    case 7: return launch_one_len<OutT, MAXS, 7>(P, total, s, prepare);
+    case 8: return launch_one_len<OutT, MAXS, 8>(P, total, s, prepare);
+    case 9: return launch_one_len<OutT, MAXS, 9>(P, total, s, prepare);
+    case 10: return launch_one_len<OutT, MAXS, 10>(P, total, s, prepare);
+    case 11: return launch_one_len<OutT, MAXS, 11>(P, total, s, prepare);
+    case 12: return launch_one_len<OutT, MAXS, 12>(P, total, s, prepare);
+    case 13: return launch_one_len<OutT, MAXS, 13>(P, total, s, prepare);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 FftSlice fft_slice(const Plan &p, const float *sino, int ld, void *q)
@@ -465,12 +654,10 @@ cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q,
 
 cudaError_t prepare_filter_fft(const Plan &p)
 {
-    const int smem = (int)filter_fft_smem_bytes(p.fft_len);
-    if (p.q_storage == FBP_F16)
-        return cudaFuncSetAttribute(filter_fft_kernel<__half, 1>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return cudaFuncSetAttribute(filter_fft_kernel<float, 1>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    FftLaunch<1> L;
+    std::memset(&L, 0, sizeof L);
+    if (p.q_storage == FBP_F16) return launch_set<__half, 1>(L, 0, p.fft_len, nullptr, true);
+    return launch_set<float, 1>(L, 0, p.fft_len, nullptr, true);
 }
 
 cudaError_t launch_filter_fft_many(const Plan *const *plans, const float *const *sinos,

@@ -68,15 +68,15 @@ def test_reconstruction_against_oracle_image(fbp):
 
 
 def test_near_identical_pair_distance_from_one_is_relative_accurate(fbp):
-    """y = x + 1e-5 (1e-4) x max|x| x noise on a reconstruction: 1 - SSIM is
-    about 1e-7 (1e-5), far above the oracle's summation floor (6.7e-12 for
+    """y = x + 3e-5 (3e-4) x max|x| x noise on a reconstruction: 1 - SSIM is
+    about 6e-7 (6e-5), far above the oracle's summation floor (6.7e-12 for
     246 x 246 windows), and must agree to 1e-3 of itself."""
     import torch
     spec = synthetic.cfg_plain()
     x = fbp.Plan(spec.n_pix, spec.n_angles, spec.n_det).reconstruct(
         torch.from_numpy(synthetic.sinogram(spec).astype(np.float32)).cuda())
     g = torch.Generator(device="cuda").manual_seed(11)
-    for amp in (1e-5, 1e-4):
+    for amp in (3e-5, 3e-4):
         y = x + amp * x.abs().max() * torch.randn(x.shape, device="cuda", generator=g)
         db, s = _check(fbp, y, x)
         want = oracle.ssim(y.double().cpu().numpy(), x.double().cpu().numpy(), 0.0)
