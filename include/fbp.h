@@ -97,6 +97,14 @@ typedef struct {
                          incident intensity i0, and every filter route converts them
                          as it loads them, p = -ln(max(I, 1) / i0) (Eq. 1,
                          Lambert-Beer; one count is the floor).  Must be finite. */
+    int point_pairs;  /* backprojection work items as pairs of tiles mirrored through
+                         the image centre, a pixel and its partner computed from one
+                         detector position (they sit at u and n_det - 1 - u): 0 = auto
+                         (on when the plan can and one slice has at least four tiles
+                         per SM), 1 = on when the plan can, -1 = off.  A plan can when
+                         n_pix is a multiple of both tile sides, the tile grid is not
+                         odd in both directions, and the sum is plain (not Kahan).
+                         The images differ from those without in the last bits only. */
 } fbp_options;
 
 /* Fill *opt with the defaults listed above. */

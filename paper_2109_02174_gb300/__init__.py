@@ -61,7 +61,8 @@ class fbp_server_stats(ctypes.Structure):
 class fbp_options(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in
                 ("dtype", "q_storage", "accumulate", "filter_path", "fft_len",
-                 "tile_x", "tile_y", "angle_chunk")] + [("i0", ctypes.c_double)]
+                 "tile_x", "tile_y", "angle_chunk")] + [("i0", ctypes.c_double),
+                                                        ("point_pairs", ctypes.c_int)]
 
 
 class fbp_fdk_geometry(ctypes.Structure):

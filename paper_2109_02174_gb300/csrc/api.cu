@@ -132,6 +132,15 @@ bool encode_rows_map_3d(const void *q, int row_floats, int pitch, int rows, int 
     return true;
 }
 
+int tiles_of(const Plan &p)
+{
+    const int tx = 8 * p.bp_wx, ty = 32 * p.bp_wy;
+    return ((p.n + tx - 1) / tx) * ((p.n + ty - 1) / ty);
+}
+
+// Backprojection work items of one slice: tiles, or tile pairs.
+int items_of(const Plan &p) { return p.bp_point_pairs ? tiles_of(p) / 2 : tiles_of(p); }
+
 BpSlice slice_desc(const Plan &p, float *image)
 {
     BpSlice s;
@@ -142,17 +151,13 @@ BpSlice slice_desc(const Plan &p, float *image)
     s.A = p.A;
     s.wp = p.bp_wp;
     s.tiles_x = (p.n + 8 * p.bp_wx - 1) / (8 * p.bp_wx);
+    s.tiles = tiles_of(p);
     s.scale = p.scale32;
     s.half_n = 0.5 * (double)(p.n - 1);
     s.half_d = 0.5 * (double)(p.D - 1);
     return s;
 }
 
-int tiles_of(const Plan &p)
-{
-    const int tx = 8 * p.bp_wx, ty = 32 * p.bp_wy;
-    return ((p.n + tx - 1) / tx) * ((p.n + ty - 1) / ty);
-}
 
 BpConfig bp_config(const Plan &p)
 {
@@ -163,6 +168,7 @@ BpConfig bp_config(const Plan &p)
     c.group = 1;
     c.half_pairs = p.q_storage == FBP_F16;
     c.kahan = p.accumulate == FBP_ACC_KAHAN;
+    c.point_pairs = p.bp_point_pairs != 0;
     return c;
 }
 
@@ -173,7 +179,7 @@ cudaError_t backproject_slice(const Plan &p, const void *q, float *image, cudaSt
     if (!encode_pairs_map(p, q, &L.maps[0])) return cudaErrorInvalidValue;
     L.slices[0] = slice_desc(p, image);
     L.n_slices = 1;
-    L.n_items = tiles_of(p);
+    L.n_items = items_of(p);
     L.tile_end[0] = L.n_items;
     L.wp_max = p.bp_wp;
     L.status = p.d_status;
@@ -487,6 +493,23 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     // the 15 shapes of the uneven 64-slice batch (each for its own count and for
     // a batch of 64); one stage barrier per 32 angles
     p->bp_chunk = o.angle_chunk ? o.angle_chunk : 32;
+    // Point-symmetric tile pairs: the tiling must map onto itself under the
+    // point reflection (n a multiple of both tile sides, no tile its own
+    // partner) and the sum be plain.  Auto: on when one slice has at least four
+    // tiles per SM, so a slice alone still gives every SM two pair items.
+    if (o.point_pairs < -1 || o.point_pairs > 1) {
+        delete p;
+        set_error("fbp_plan: point_pairs %d is not -1, 0 or 1", o.point_pairs);
+        return FBP_ERR_INVALID_ARG;
+    }
+    {
+        const int tx = 8 * p->bp_wx, ty = 32 * p->bp_wy;
+        const int gx = n_pix / tx, gy = n_pix / ty;
+        const bool can = o.dtype == FBP_F32 && o.accumulate == FBP_ACC_PLAIN &&
+                         n_pix % tx == 0 && n_pix % ty == 0 && !((gx & 1) && (gy & 1));
+        const bool want = o.point_pairs > 0 || (o.point_pairs == 0 && (long)gx * gy >= 4L * sms);
+        p->bp_point_pairs = (can && want) ? 1 : 0;
+    }
 
     std::vector<double> taps;
     make_taps((int)filter, n_det, det_spacing, taps);

@@ -47,9 +47,9 @@ std::string bucket_key(int n, int A, int D, double tau, int filter, const fbp_op
                        int batch)
 {
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%.9g|%d|%d|%d|%d|%d|%dx%dx%d|%d", gpu_name().c_str(), n,
-             A, D, tau, filter, b.dtype, b.q_storage, b.accumulate, b.filter_path, b.tile_x,
-             b.tile_y, b.angle_chunk, batch);
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%.9g|%d|%d|%d|%d|%d|%dx%dx%d|%d|pp%d",
+             gpu_name().c_str(), n, A, D, tau, filter, b.dtype, b.q_storage, b.accumulate,
+             b.filter_path, b.tile_x, b.tile_y, b.angle_chunk, batch, b.point_pairs);
     return buf;
 }
 
@@ -150,6 +150,8 @@ fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
         out->options.dtype = b.dtype;
         out->options.q_storage = b.q_storage;
         out->options.accumulate = b.accumulate;
+        out->options.point_pairs = b.point_pairs;
+        out->options.i0 = b.i0;
         out->from_cache = 1;
         return FBP_OK;
     }
@@ -244,6 +246,8 @@ fbp_status fbp_autotune(int n_pix, int n_angles, int n_det, double det_spacing,
     best.options.dtype = b.dtype;
     best.options.q_storage = b.q_storage;
     best.options.accumulate = b.accumulate;
+    best.options.point_pairs = b.point_pairs;
+    best.options.i0 = b.i0;
     best.from_cache = 0;
     g_cache[key] = best;
     save_line(key, best);

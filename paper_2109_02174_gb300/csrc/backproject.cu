@@ -30,6 +30,14 @@
 // Every pixel sums its angles in order 0..A-1 in registers: no atomics, no
 // cross-CTA reduction, the same bits on every run and in every batch.
 //
+// Point pairs (plans whose tiling is point-symmetric about the image centre):
+// a work item is a tile and its mirror image through the centre, and each
+// consumer thread computes a pixel and its mirrored partner from one detector
+// position, which takes the position, rounding and fraction off the FP32 pipe
+// for half of the updates (the same saving two slices of a batch get from
+// sharing them).  A plan uses them in every path (alone, batched, served), so
+// its results are the same bits everywhere.
+//
 // Every mbarrier wait is bounded (the run-time limit of WaitHook).  A consumer
 // whose wait runs out records FBP_ERR_TIMEOUT and leaves; a producer whose
 // wait for a free stage runs out records it, waits (bounded again) for the
@@ -90,6 +98,7 @@ struct Layout {
     int prm;    // offset of params [NSTAGE][CH] float4
     int full;   // offset of full barriers [NSTAGE]
     int empty;  // offset of empty barriers [NSTAGE]
+    int items;  // offset of the work item of each stage [NSTAGE] int
     int total;  // bytes including 128 of alignment slack
     __host__ __device__ static Layout make(int wp_max, int pair_bytes, int group)
     {
@@ -99,12 +108,14 @@ struct Layout {
         L.prm = NSTAGE * L.stage;
         L.full = L.prm + NSTAGE * CH * 16;
         L.empty = L.full + NSTAGE * 8;
-        L.total = L.empty + NSTAGE * 8 + 128;
+        L.items = L.empty + NSTAGE * 8;
+        L.total = L.items + NSTAGE * 4 + 128;
         return L;
     }
 };
 
-// Work item -> (slice, tile) through the prefix sums of the slices' tile counts.
+// Work item -> (slice, item within the slice) through the prefix sums of the
+// slices' item counts.
 template <int MAXS>
 __device__ __forceinline__ int2 item_of(const BpLaunch<MAXS> &P, int item)
 {
@@ -122,11 +133,20 @@ __device__ __forceinline__ int2 item_of(const BpLaunch<MAXS> &P, int item)
 // for eight CTAs per SM: batched 64 x 512^2 x 720 at tile 32x32 / 32 angles
 // per stage 4547 vs 3935 Gupdates/s, one 512^2 slice 2866 vs 1998, one 2048^2
 // slice 3746 vs 3643; the cap for eight CTAs was never faster.
-template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS>
+//
+// G rows of window per angle and stage: G = 1, one tile of one slice; G = 2,
+// either the same tile of two slices of one plan (PP = false) or, with point
+// pairs (PP = true), a tile A and its point-symmetric partner B of one slice.
+// A pixel at (x, y) and its partner at (-x, -y) have detector coordinates u and
+// n_det - 1 - u, so the partner's pair index within B's window is K - j (K per
+// tile pair and angle, from the two window starts) and its weight is -w: one
+// position computation serves both pixels.
+template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS, bool PP>
 __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     bp_persistent_kernel(const __grid_constant__ BpLaunch<MAXS> P)
 {
-    static_assert(G == 1 || (G == 2 && !KAHAN), "two-slice items are plain-sum only");
+    static_assert(G == 1 || (G == 2 && !KAHAN), "two-row items are plain-sum only");
+    static_assert(!PP || G == 2, "point pairs stage two rows per angle");
     constexpr int NCW = WX * WY;           // consumer warps
     constexpr int TX = 8 * WX;             // tile width  (warp footprint 8 wide)
     constexpr int TY = 32 * WY;            // tile height (warp covers 32 rows)
@@ -141,6 +161,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     const uint32_t base_addr = (smem_addr(smem) + 127u) & ~127u;
     unsigned char *base_ptr = smem + (base_addr - smem_addr(smem));
     float4 *prm = reinterpret_cast<float4 *>(base_ptr + L.prm);
+    volatile int *stage_items = reinterpret_cast<volatile int *>(base_ptr + L.items);
     const uint32_t full0 = base_addr + (uint32_t)L.full;
     const uint32_t empty0 = base_addr + (uint32_t)L.empty;
 
@@ -156,11 +177,6 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     }
     __syncthreads();
 
-    // The work item a stage belongs to rides in the otherwise unused w of the
-    // stage's first angle parameters (-1: no more work).
-    auto stage_item = [&](int s) -> volatile float & {
-        return reinterpret_cast<volatile float *>(prm + s * CH)[3];
-    };
     // single-slice launches (MAXS = 1) always stride: no counter code in them
     const bool dyn = MAXS > 1 && P.sched != nullptr;
     const WaitHook hook = g_wait_hook;
@@ -170,10 +186,10 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
         // ------------------------------------------------------------ producer
         // The next work item comes from the launch's counter (P.sched: taken
         // when the ring has room for the item's first stage, so a CTA that
-        // started late or drew cheap items takes more; the first stage of
-        // every item carries its index for the consumers, and a stage
-        // carrying -1 ends their loop) or, without one, by striding (b,
-        // b + grid, ...), which the consumers follow on their own.
+        // started late or drew cheap items takes more; every stage records its
+        // item for the consumers, and a stage recording -1 ends their loop) or,
+        // without one, by striding (b, b + grid, ...), which the consumers
+        // follow on their own.
         const int withhold = withheld_stage(hook, kWithholdBackproject, blockIdx.x == 0);
         auto wait_empty = [&](uint32_t i) -> bool {
             const uint32_t use = i / NSTAGE;
@@ -209,7 +225,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             if (item >= P.n_items) {
                 if (lane == 0) {
                     const int s = (int)(it % NSTAGE);
-                    stage_item(s) = __int_as_float(-1);
+                    stage_items[s] = -1;
                     mbar_arrive(full0 + 8u * s);  // no bytes: completes the phase
                     // the last CTA past the end leaves the counter at zero for
                     // the next launch that uses it
@@ -225,6 +241,10 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
             const double x0 = (double)(tx * TX) - S.half_n;
             const double y0 = (double)(ty * TY) - S.half_n;
+            // point pairs: the partner tile's origin (tile tiles - 1 - item)
+            const int tb = S.tiles - 1 - wi.y;
+            const double x0b = (double)((tb % S.tiles_x) * TX) - S.half_n;
+            const double y0b = (double)((tb / S.tiles_x) * TY) - S.half_n;
             const int nch = (S.A + CH - 1) / CH;
             for (int cc = 0; cc < nch; ++cc, ++it) {
                 const int s = (int)(it % NSTAGE);
@@ -234,20 +254,28 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 }
                 const int a0 = cc * CH;
                 const int na = min(CH, S.A - a0);
-                int pb = 0;
+                int pb = 0, pbb = 0;
                 if (lane < na) {
                     const double2 cs = S.trig64[a0 + lane];
+                    const double ex = fmin(0.0, (double)(TX - 1) * cs.x) +
+                                      fmin(0.0, (double)(TY - 1) * cs.y);
                     const double u0 = x0 * cs.x + y0 * cs.y + S.half_d;
-                    const double umin = u0 + fmin(0.0, (double)(TX - 1) * cs.x) +
-                                        fmin(0.0, (double)(TY - 1) * cs.y);
                     // first pair of the window: pair p holds bin k = p - 1; start
                     // one bin below floor(umin), aligned down to 16 bytes.
-                    pb = __double2int_rd(umin) & ~(TR::kAlign - 1);
+                    pb = __double2int_rd(u0 + ex) & ~(TR::kAlign - 1);
                     const int base = pb - 1;  // bin of the window's first pair
+                    int w4 = 0;
+                    if constexpr (PP) {
+                        const double u0b = x0b * cs.x + y0b * cs.y + S.half_d;
+                        pbb = __double2int_rd(u0b + ex) & ~(TR::kAlign - 1);
+                        // partner pair index K - j, K = n_det - pb - pbb
+                        w4 = (int)(2.0 * S.half_d + 1.0) - pb - pbb;
+                    }
                     prm[s * CH + lane] = make_float4((float)cs.x, (float)cs.y,
                                                      (float)(u0 - (double)base - 0.5),
-                                                     __int_as_float(item));
+                                                     __int_as_float(w4));
                 }
+                if (lane == 0) stage_items[s] = item;
                 __syncwarp();
                 // (tests only: a withheld stage gets neither its arrival nor its loads)
                 const bool fill = (int)it != withhold;
@@ -257,12 +285,17 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 }
                 __syncwarp();
                 // each lane issues its own angle's load(s) (x in elements of PairT);
-                // slice g of the item lands in rows g*CH .. g*CH + CH-1 of the stage
+                // row g of the item lands in rows g*CH .. g*CH + CH-1 of the stage
                 if (lane < na && fill) {
 #pragma unroll
-                    for (int g = 0; g < G; ++g)
+                    for (int g = 0; g < G; ++g) {
+                        // two slices: the same window of each slice's rows; point
+                        // pairs: the partner tile's window of the one slice
+                        const int xg = (PP && g) ? pbb : pb;
                         tma_load_2d(base_addr + (uint32_t)(s * L.stage + (g * CH + lane) * L.row),
-                                    &P.maps[G * wi.x + g], 2 * pb, a0 + lane, full0 + 8u * s);
+                                    &P.maps[PP ? wi.x : G * wi.x + g], 2 * xg, a0 + lane,
+                                    full0 + 8u * s);
+                    }
                 }
             }
             if (!dyn) item += gridDim.x;
@@ -293,7 +326,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
                 return;
             }
-            item = __float_as_int(stage_item((int)(it % NSTAGE)));
+            item = stage_items[it % NSTAGE];
             if (item < 0) break;
         } else if (item >= P.n_items) {
             break;
@@ -325,6 +358,10 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 const float4 p = pp[a];
                 const uint32_t cb =
                     stage_addr + (uint32_t)(a * L.row) - (kMagicBits << TR::kShift);
+                // point pairs: the partner reads pair K - j of its row (CH rows on)
+                const uint32_t cbb = stage_addr + (uint32_t)((CH + a) * L.row) +
+                                     ((uint32_t)__float_as_int(p.w) << TR::kShift) +
+                                     (kMagicBits << TR::kShift);
                 const float xc = fmaf(lxf, p.x, p.z);
                 const float2 xc2 = make_float2(xc, xc);
                 const float2 s2 = make_float2(p.y, p.y);
@@ -338,17 +375,28 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     const uint32_t o1 = (__float_as_uint(t.y) << TR::kShift) + cb;
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
-                        const uint32_t go = (uint32_t)(g * CH * L.row);
+                        uint32_t a0, a1;
+                        if constexpr (PP) {
+                            a0 = g ? cbb - (__float_as_uint(t.x) << TR::kShift) : o0;
+                            a1 = g ? cbb - (__float_as_uint(t.y) << TR::kShift) : o1;
+                        } else {
+                            const uint32_t go = (uint32_t)(g * CH * L.row);
+                            a0 = o0 + go;
+                            a1 = o1 + go;
+                        }
                         float2 q0, q1;
                         if constexpr (TR::kBytes == 8) {
-                            q0 = lds_f2(o0 + go);
-                            q1 = lds_f2(o1 + go);
+                            q0 = lds_f2(a0);
+                            q1 = lds_f2(a1);
                         } else {
-                            q0 = lds_h2_as_f2(o0 + go);
-                            q1 = lds_h2_as_f2(o1 + go);
+                            q0 = lds_h2_as_f2(a0);
+                            q1 = lds_h2_as_f2(a1);
                         }
-                        const float v0 = fmaf(w.x, q0.y, q0.x);
-                        const float v1 = fmaf(w.y, q1.y, q1.x);
+                        // the partner's weight is -w
+                        const float wx = (PP && g) ? -w.x : w.x;
+                        const float wy = (PP && g) ? -w.y : w.y;
+                        const float v0 = fmaf(wx, q0.y, q0.x);
+                        const float v1 = fmaf(wy, q1.y, q1.x);
                         if constexpr (KAHAN) {
                             const float y0 = v0 - cmp[2 * jj];
                             const float t0 = acc[0][2 * jj] + y0;
@@ -369,15 +417,27 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             if (lane == 0) mbar_arrive(empty0 + 8u * s);
         }
 
-        const int col = tx * TX + lx;
-        if (col < S.n) {
+        if constexpr (PP) {
+            // tile A and, mirrored through the image centre, its partner
+            // (tilings with n a multiple of the tile: every pixel is inside)
+            const int col = tx * TX + lx;
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                float *img = g ? S.image2 : S.image;
+            for (int j = 0; j < PPT; ++j) {
+                const int row = ty * TY + ly0 + 4 * j;
+                S.image[(size_t)row * S.n + col] = acc[0][j] * S.scale;
+                S.image[(size_t)(S.n - 1 - row) * S.n + (S.n - 1 - col)] = acc[1][j] * S.scale;
+            }
+        } else {
+            const int col = tx * TX + lx;
+            if (col < S.n) {
 #pragma unroll
-                for (int j = 0; j < PPT; ++j) {
-                    const int row = ty * TY + ly0 + 4 * j;
-                    if (row < S.n) img[(size_t)row * S.n + col] = acc[g][j] * S.scale;
+                for (int g = 0; g < G; ++g) {
+                    float *img = g ? S.image2 : S.image;
+#pragma unroll
+                    for (int j = 0; j < PPT; ++j) {
+                        const int row = ty * TY + ly0 + 4 * j;
+                        if (row < S.n) img[(size_t)row * S.n + col] = acc[g][j] * S.scale;
+                    }
                 }
             }
         }
@@ -385,12 +445,12 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     }
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS, bool PP>
 cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
 {
     using L_t = Layout<bp_stages(CH, G), CH>;
     const L_t L = L_t::make(P.wp_max, PairTraits<PairT>::kBytes, G);
-    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, CH, G, MAXS>;
+    auto kern = bp_persistent_kernel<PairT, KAHAN, WX, WY, CH, G, MAXS, PP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          L.total);
     if (e != cudaSuccess) return e;
@@ -410,31 +470,41 @@ cudaError_t launch_one(const BpLaunch<MAXS> &P, int grid_limit, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename PairT, bool KAHAN, int WX, int WY, int G, int MAXS>
+template <typename PairT, bool KAHAN, int WX, int WY, int G, int MAXS, bool PP>
 cudaError_t by_chunk(const BpLaunch<MAXS> &P, int chunk, int grid_limit, cudaStream_t s)
 {
-    if (chunk == 8) return launch_one<PairT, KAHAN, WX, WY, 8, G, MAXS>(P, grid_limit, s);
-    if (chunk == 32) return launch_one<PairT, KAHAN, WX, WY, 32, G, MAXS>(P, grid_limit, s);
-    if (chunk == 16) return launch_one<PairT, KAHAN, WX, WY, 16, G, MAXS>(P, grid_limit, s);
+    if (chunk == 8) return launch_one<PairT, KAHAN, WX, WY, 8, G, MAXS, PP>(P, grid_limit, s);
+    if (chunk == 32) return launch_one<PairT, KAHAN, WX, WY, 32, G, MAXS, PP>(P, grid_limit, s);
+    if (chunk == 16) return launch_one<PairT, KAHAN, WX, WY, 16, G, MAXS, PP>(P, grid_limit, s);
     return cudaErrorInvalidValue;
 }
 
 template <int WX, int WY, int MAXS>
 cudaError_t by_variant(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit, cudaStream_t s)
 {
+    if (c.point_pairs) {
+        // one slice per item, a tile and its partner (plain sums)
+        if (c.kahan || c.group != 1) return cudaErrorInvalidValue;
+        if (!c.half_pairs)
+            return by_chunk<float, false, WX, WY, 2, MAXS, true>(P, c.chunk, grid_limit, s);
+        return by_chunk<__half, false, WX, WY, 2, MAXS, true>(P, c.chunk, grid_limit, s);
+    }
     if (c.group == 2) {
         if constexpr (MAXS > 1) {
             if (c.kahan) return cudaErrorInvalidValue;
             if (!c.half_pairs)
-                return by_chunk<float, false, WX, WY, 2, MAXS>(P, c.chunk, grid_limit, s);
-            return by_chunk<__half, false, WX, WY, 2, MAXS>(P, c.chunk, grid_limit, s);
+                return by_chunk<float, false, WX, WY, 2, MAXS, false>(P, c.chunk, grid_limit, s);
+            return by_chunk<__half, false, WX, WY, 2, MAXS, false>(P, c.chunk, grid_limit, s);
         }
         return cudaErrorInvalidValue;
     }
-    if (!c.half_pairs && !c.kahan) return by_chunk<float, false, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
-    if (!c.half_pairs && c.kahan) return by_chunk<float, true, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
-    if (c.half_pairs && !c.kahan) return by_chunk<__half, false, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
-    return by_chunk<__half, true, WX, WY, 1, MAXS>(P, c.chunk, grid_limit, s);
+    if (!c.half_pairs && !c.kahan)
+        return by_chunk<float, false, WX, WY, 1, MAXS, false>(P, c.chunk, grid_limit, s);
+    if (!c.half_pairs && c.kahan)
+        return by_chunk<float, true, WX, WY, 1, MAXS, false>(P, c.chunk, grid_limit, s);
+    if (c.half_pairs && !c.kahan)
+        return by_chunk<__half, false, WX, WY, 1, MAXS, false>(P, c.chunk, grid_limit, s);
+    return by_chunk<__half, true, WX, WY, 1, MAXS, false>(P, c.chunk, grid_limit, s);
 }
 
 template <int MAXS>

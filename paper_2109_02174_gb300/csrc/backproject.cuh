@@ -26,7 +26,7 @@ struct BpSlice {
     int wp;       // detector window per tile and angle, in (mid, slope) pairs
     int tiles_x;  // tiles per image row
     float scale;  // pi / A
-    int pad_;
+    int tiles;    // tiles of the slice (work items: tiles, or tiles / 2 for point pairs)
     double half_n;  // (n - 1) / 2
     double half_d;  // (n_det - 1) / 2
 };
@@ -60,6 +60,7 @@ struct BpConfig {
     bool half_pairs;  // FP16-stored (mid, slope) pairs
     bool kahan;       // Kahan-compensated sum over angles
     int group;        // slices per work item: 1, or 2 (same plan, not Kahan)
+    bool point_pairs; // work item = a tile and its point-symmetric partner (one slice)
 };
 
 // The kernel configuration of a plan's slices (api.cu).

@@ -17,7 +17,7 @@
 
 namespace fbp {
 BpSlice slice_desc(const Plan &p, float *image);
-int tiles_of(const Plan &p);
+int items_of(const Plan &p);
 BpConfig bp_config(const Plan &p);
 }  // namespace fbp
 
@@ -157,7 +157,8 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
     std::map<std::tuple<int, int, int, int>, std::vector<int>> by_cfg;
     for (int i = 0; i < n; ++i) {
         const BpConfig c = bp_config(*plans[i]);
-        by_cfg[std::make_tuple(c.wx, c.wy, (int)c.half_pairs, (int)c.kahan)].push_back(i);
+        by_cfg[std::make_tuple(c.wx, c.wy, (int)c.half_pairs,
+                               (int)c.kahan + 2 * (int)c.point_pairs)].push_back(i);
     }
     std::unique_ptr<BpLaunch<kBpMaxSlices>> L(new BpLaunch<kBpMaxSlices>());
     int launches = 0;
@@ -174,10 +175,11 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
                          [&](int a, int c) { return plans[a]->A > plans[c]->A; });
         const BpConfig cfg = bp_config(*plans[members[0]]);
         // Slices of one plan share every index computation: pair them into
-        // two-slice items (plain sums only); the rest stay single.
+        // two-slice items (plain sums only); the rest stay single.  Plans with
+        // point-symmetric tile pairs share it within each slice instead.
         std::vector<std::pair<int, int>> pairs;
         std::vector<int> singles;
-        if (!cfg.kahan) {
+        if (!cfg.kahan && !cfg.point_pairs) {
             std::map<const Plan *, std::vector<int>> by_plan;
             for (int i : members) by_plan[plans[i]].push_back(i);
             std::vector<bool> paired((size_t)n, false);
@@ -218,7 +220,7 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
                             return cudaErrorInvalidValue;
                         L->slices[m].image2 = static_cast<float *>(io[j].image);
                     }
-                    acc += tiles_of(p);
+                    acc += items_of(p);
                     L->tile_end[m] = acc;
                     L->wp_max = std::max(L->wp_max, p.bp_wp);
                 }

@@ -48,6 +48,7 @@ struct Plan {
     int bp_wy;
     int bp_wp;
     int bp_chunk;  // angles per shared-memory stage (8, 16, 32)
+    int bp_point_pairs;  // 1: work items are point-symmetric tile pairs (backproject.cu)
     double i0;       // > 0: the sinogram holds intensities, converted on load (Eq. 1)
     float i0f;
     float ln_i0f;    // ln(i0) (FP64, rounded)

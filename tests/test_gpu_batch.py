@@ -294,3 +294,29 @@ def test_kernel_count_of_a_same_plan_batch(fbp):
     sinos = [_sino(synthetic.SliceSpec(n, A, D, 4, seed=990 + i)) for i in range(4)]
     batch = fbp.Batch([plan] * 4, sinos)
     assert batch.kernel_count == 2
+
+
+def test_point_pair_plans_in_batches_bitwise(fbp):
+    """Slices of point-pair plans (a tile and its mirror image per work item)
+    batched with other plans: each image equals its alone result bit for bit,
+    and the batch launch takes the counter hand-out like the others."""
+    import torch
+    n, A = 128, 90
+    D = synthetic.det_for(n)
+    pp = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=1)
+    pp16 = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=1, q_storage=2)
+    plain = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=-1)
+    plans = [pp, pp, pp, plain, plain, pp16, fbp.Plan(256, 120, synthetic.det_for(256),
+                                                       tile_x=8, tile_y=32, point_pairs=1)]
+    specs = [synthetic.SliceSpec(p.n_pix, p.n_angles, p.n_det, 6, seed=1200 + i)
+             for i, p in enumerate(plans)]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch(plans, sinos)
+    for _ in range(2):
+        for im in batch.images:
+            im.fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        batch.status()
+        for plan, sino, img in zip(plans, sinos, batch.images):
+            assert np.array_equal(img.cpu().numpy(), _alone(fbp, plan, sino))

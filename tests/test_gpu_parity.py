@@ -474,3 +474,50 @@ def test_maximum_sizes_direct_route(fbp):
     ref = oracle.backproject_pixels(Q, th, 1.0, n, rows, cols)
     got = img[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
     assert_parity(got.astype(np.float64), ref)
+
+
+# ---------------------------------------------------------------- point-symmetric tile pairs
+@pytest.mark.parametrize("geom", [
+    dict(n=256, A=180, D=363, tile=(8, 32)),
+    dict(n=128, A=90, D=183, tile=(32, 32)),
+    dict(n=128, A=45, D=120, tau=1.6, tile=(32, 64)),
+    dict(n=64, A=50, D=120, tau=0.8, tile=(32, 32)),
+    dict(n=192, A=120, D=273, tile=(32, 32), q_storage=2),
+])
+def test_point_pairs_match_oracle(fbp, geom):
+    """Plans whose work items are tile pairs mirrored through the image centre
+    (one detector position per pixel and partner) meet the bars; their image
+    differs from the unpaired plan's only by rounding."""
+    g = dict(geom)
+    n, A, D = g.pop("n"), g.pop("A"), g.pop("D")
+    tau = g.pop("tau", 1.0)
+    tx, ty = g.pop("tile")
+    spec = synthetic.SliceSpec(n, A, D, 8, seed=77 + n + A, tau=tau)
+    th = synthetic.default_angles(A)
+    sino32 = synthetic.sinogram(spec, th).astype(np.float32)
+    imgs = {}
+    for pp in (1, -1):
+        plan = fbp.Plan(n, A, D, det_spacing=tau, tile_x=tx, tile_y=ty, point_pairs=pp, **g)
+        imgs[pp] = _np(plan.reconstruct(_t(sino32)))
+        plan.device_status()
+    assert not np.array_equal(imgs[1], imgs[-1])  # the paired path ran
+    ref = oracle.fbp(sino32.astype(np.float64), th, tau, 0, n, nthreads=NTHREADS)
+    if g.get("q_storage") == 2:
+        e_max, e_rms = errors(imgs[1], ref)
+        assert e_max < 5e-3 and e_rms < 1e-3
+        e2 = errors(imgs[-1], ref)
+        assert abs(e_max - e2[0]) < 0.5 * e2[0] + 1e-6
+    else:
+        assert_parity(imgs[1], ref)
+
+
+def test_point_pairs_fall_back_where_the_tiling_is_not_symmetric(fbp):
+    """n not a multiple of the tile, or a tile grid odd in both directions
+    (96 x 96 in 32 x 32 tiles: the centre tile is its own partner): the plan
+    keeps single-tile items, the same bits as with the option off."""
+    for n, (tx, ty) in ((100, (32, 32)), (96, (32, 32))):
+        A, D = 60, synthetic.det_for(n)
+        sino = _t(synthetic.sinogram(synthetic.SliceSpec(n, A, D, 6, seed=n)))
+        a = _np(fbp.Plan(n, A, D, tile_x=tx, tile_y=ty, point_pairs=1).reconstruct(sino))
+        b = _np(fbp.Plan(n, A, D, tile_x=tx, tile_y=ty, point_pairs=-1).reconstruct(sino))
+        assert np.array_equal(a, b), n
