@@ -99,12 +99,14 @@ typedef struct {
                          Lambert-Beer; one count is the floor).  Must be finite. */
     int point_pairs;  /* backprojection work items as pairs of tiles mirrored through
                          the image centre, a pixel and its partner computed from one
-                         detector position (they sit at u and n_det - 1 - u): 0 = auto
-                         (on when the plan can and one slice has at least four tiles
-                         per SM), 1 = on when the plan can, -1 = off.  A plan can when
-                         n_pix is a multiple of both tile sides, the tile grid is not
-                         odd in both directions, and the sum is plain (not Kahan).
-                         The images differ from those without in the last bits only. */
+                         detector position (they sit at u and n_det - 1 - u): 0 = auto,
+                         1 = on when the plan can, -1 = off.  A plan can when n_pix is
+                         a multiple of both tile sides, the tile grid is not odd in
+                         both directions, and the sum is plain (not Kahan).  Auto
+                         applies to the automatic tile only (tile_x = tile_y = 0): it
+                         takes pairs on 32 x 32 tiles when one slice has at least 7/4
+                         tiles of 32 x 64 per SM (n_pix > 704 on 152 SMs).  The images
+                         differ from those without pairs in the last bits only. */
 } fbp_options;
 
 /* Fill *opt with the defaults listed above. */

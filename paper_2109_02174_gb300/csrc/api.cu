@@ -475,6 +475,26 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         if (2 * tiles >= (long)sms) break;
     }
     if (pick < 0 && o.dtype == FBP_F64) pick = 0;  // the FP64 path has no tiles
+    // Point-symmetric tile pairs (see below) on the automatic tile: the
+    // tiling must map onto itself under the reflection through the image
+    // centre (n a multiple of both tile sides, the grid not odd in both
+    // directions) and the sum be plain.  Auto (option 0) takes them, on 32 x 32
+    // tiles, for a slice of at least 7/4 tiles of 32 x 64 per SM; one slice,
+    // microseconds, without / with pairs: 512^2 x 720 at 32 x 32: 72.3 / 84.6;
+    // 768^2 x 1440 at 32 x 64: 240 / 214, at 32 x 32: 249 / 216;
+    // 1024^2 x 1440: 469 / 418, 484 / 425; 1536^2 x 1024: 664 / 591,
+    // 687 / 570; 2048^2 x 2048: 2293 / 2040, 2380 / 1934.
+    auto pairs_fit = [&](int tx, int ty) {
+        const int gx = n_pix / tx, gy = n_pix / ty;
+        return o.dtype == FBP_F32 && o.accumulate == FBP_ACC_PLAIN && n_pix % tx == 0 &&
+               n_pix % ty == 0 && !((gx & 1) && (gy & 1));
+    };
+    const long tiles_big = (long)((n_pix + 31) / 32) * (long)((n_pix + 63) / 64);
+    const bool pairs_auto = o.point_pairs == 0 && 4 * tiles_big >= 7L * sms;
+    if (pick >= 0 && !largest && !o.tile_x && !o.tile_y && o.point_pairs >= 0 &&
+        (pairs_auto || o.point_pairs > 0) && pairs_fit(32, 32) &&
+        window_pairs(trig, 32, 32, align) <= 128)
+        pick = 1;  // 32 x 32
     if (pick < 0) {
         delete p;
         set_error("fbp_plan: no backprojection tile fits the detector window (det_spacing %.3g, "
@@ -493,21 +513,18 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     // the 15 shapes of the uneven 64-slice batch (each for its own count and for
     // a batch of 64); one stage barrier per 32 angles
     p->bp_chunk = o.angle_chunk ? o.angle_chunk : 32;
-    // Point-symmetric tile pairs: the tiling must map onto itself under the
-    // point reflection (n a multiple of both tile sides, no tile its own
-    // partner) and the sum be plain.  Auto: on when one slice has at least four
-    // tiles per SM, so a slice alone still gives every SM two pair items.
+    // Point-symmetric tile pairs: explicit (option 1) wherever the tiling
+    // allows; automatic only with the automatic tile (tuned, batch and serving
+    // plans name their tile and keep single-tile items unless asked).
     if (o.point_pairs < -1 || o.point_pairs > 1) {
         delete p;
         set_error("fbp_plan: point_pairs %d is not -1, 0 or 1", o.point_pairs);
         return FBP_ERR_INVALID_ARG;
     }
     {
-        const int tx = 8 * p->bp_wx, ty = 32 * p->bp_wy;
-        const int gx = n_pix / tx, gy = n_pix / ty;
-        const bool can = o.dtype == FBP_F32 && o.accumulate == FBP_ACC_PLAIN &&
-                         n_pix % tx == 0 && n_pix % ty == 0 && !((gx & 1) && (gy & 1));
-        const bool want = o.point_pairs > 0 || (o.point_pairs == 0 && (long)gx * gy >= 4L * sms);
+        const bool can = pairs_fit(8 * p->bp_wx, 32 * p->bp_wy);
+        const bool want = o.point_pairs > 0 ||
+                          (pairs_auto && !largest && !o.tile_x && !o.tile_y);
         p->bp_point_pairs = (can && want) ? 1 : 0;
     }
 

@@ -125,3 +125,27 @@ def test_default_tile_rule(fbp):
     assert np.array_equal(img(tile_x=-1, tile_y=-1), by_tile[(32, 64)])
     assert not np.array_equal(by_tile[(32, 64)], by_tile[(8, 32)])
 
+
+
+def test_default_plan_of_a_large_slice_takes_point_pairs(fbp):
+    """From n_pix > 704 (on 152 SMs) the automatic tile is 32 x 32 with
+    point-symmetric tile pairs; a named tile keeps single-tile items unless
+    point_pairs = 1 asks for them."""
+    import torch
+    n, A = 768, 90
+    D = synthetic.det_for(n)
+    sino = torch.from_numpy(
+        synthetic.sinogram(synthetic.SliceSpec(n, A, D, 6, seed=7)).astype(np.float32)).cuda()
+
+    def img(**opt):
+        out = fbp.Plan(n, A, D, **opt).reconstruct(sino)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    paired = img(tile_x=32, tile_y=32, point_pairs=1)
+    single = img(tile_x=32, tile_y=32, point_pairs=-1)
+    assert not np.array_equal(paired, single)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if 4 * 24 * 12 >= 7 * sms:
+        assert np.array_equal(img(), paired)
+    assert np.array_equal(img(tile_x=32, tile_y=32), single)
+    assert np.array_equal(img(point_pairs=-1), img(tile_x=32, tile_y=64, point_pairs=-1))
