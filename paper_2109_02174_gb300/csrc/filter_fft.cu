@@ -28,7 +28,6 @@
 // slice after slice.
 #include "fbp_internal.h"
 #include "lambert.cuh"
-#include "ptx.cuh"
 #include "pairs.cuh"
 
 #include <cstring>
@@ -478,30 +477,6 @@ constexpr int fft_min_blocks(int L)
     return ((1 << L) / 16) >= 32 ? 512 / ((1 << L) / 16) : 16;
 }
 
-__device__ __forceinline__ void cp_async4(uint32_t dst, const float *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// The slice of launch block b (prefix sums of the slices' block counts).
-template <int MAXS>
-__device__ __forceinline__ int slice_of_block(const FftLaunch<MAXS> &P, int b)
-{
-    int lo = 0, hi = P.n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (b < P.s[mid].block_end) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-}
-
-// Persistent: CTA c takes row blocks c, c + grid, ...  While a block is
-// transformed, the sinogram values of the CTA's next block are already on
-// their way into shared memory (cp.async, each thread its own positions, so
-// no barrier is needed between copying and reading them); the loads' latency,
-// which a CTA starting cold waits for, is hidden behind the previous block.
 template <typename OutT, int MAXS, int L>
 __global__ void __launch_bounds__((1 << L) / 16, fft_min_blocks(L))
     filter_fft_kernel(const __grid_constant__ FftLaunch<MAXS> P)
@@ -509,129 +484,100 @@ __global__ void __launch_bounds__((1 << L) / 16, fft_min_blocks(L))
     constexpr int N = 1 << L;
     constexpr int T = N / 16;
     extern __shared__ float4 buf[];
-    // staging after the exchange buffer: value of row r, position t + q T
-    // (q < 8) at stg[(8 r + q) T + t]
-    float *stg = reinterpret_cast<float *>(buf + (N + N / 16));
-    const int t = threadIdx.x;
-    const int total = P.s[P.n - 1].block_end;
-
-    auto prefetch = [&](int b) {
-        if (b < total) {
-            const int si = slice_of_block(P, b);
-            const FftSlice &S = P.s[si];
-            const int i0 = 4 * (b - (si > 0 ? P.s[si - 1].block_end : 0));
-            const int rows = min(4, S.A - i0);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (r < rows) {
-                    const float *src = S.sino + (size_t)(i0 + r) * S.ld;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int j = t + q * T;
-                        if (j < S.D)
-                            cp_async4(smem_addr(stg + (8 * r + q) * T + t), src + j);
-                    }
-                }
-            }
-        }
-        cp_async_commit();
-    };
-
-    prefetch(blockIdx.x);
-    for (int b = blockIdx.x; b < total; b += gridDim.x) {
-        const int si = slice_of_block(P, b);
-        const FftSlice &S = P.s[si];
-        const int blk = b - (si > 0 ? P.s[si - 1].block_end : 0);
-        const int D = S.D;
-        const int i0 = 4 * blk;
-        const int rows = min(4, S.A - i0);  // 1..4 rows in this block
-        // rows i0, i0+1 -> transform 0 (re, im); rows i0+2, i0+3 -> transform 1.
-        // n_det <= N/2: positions t + q T with q >= 8 are zero padding
-        cp_async_wait_all();
-        C2 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int j = t + q * T;
-            v[q].re = make_float2(0.0f, 0.0f);
-            v[q].im = make_float2(0.0f, 0.0f);
-            if (q < 8 && j < D) {
-                v[q].re.x = stg[q * T + t];
-                if (rows > 1) v[q].im.x = stg[(8 + q) * T + t];
-                if (rows > 2) v[q].re.y = stg[(16 + q) * T + t];
-                if (rows > 3) v[q].im.y = stg[(24 + q) * T + t];
-            }
-        }
-        if (S.i0 > 0.0f) {
-            // intensities: converted after the loads (the padding stays zero)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (t + q * T < D) {
-                    v[q].re.x = line_integral(v[q].re.x, S.i0, S.ln_i0);
-                    if (rows > 1) v[q].im.x = line_integral(v[q].im.x, S.i0, S.ln_i0);
-                    if (rows > 2) v[q].re.y = line_integral(v[q].re.y, S.i0, S.ln_i0);
-                    if (rows > 3) v[q].im.y = line_integral(v[q].im.y, S.i0, S.ln_i0);
-                }
-            }
-        }
-        if (S.wt != nullptr) {
-            // per-element weights of the row (a cone-beam cosine weight), applied to the
-            // line integrals
-            const float *w0 = S.wt + (size_t)(i0 % S.wt_rows) * D;
-            const float *w1 = S.wt + (size_t)((i0 + 1) % S.wt_rows) * D;
-            const float *w2 = S.wt + (size_t)((i0 + 2) % S.wt_rows) * D;
-            const float *w3 = S.wt + (size_t)((i0 + 3) % S.wt_rows) * D;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int j = t + q * T;
-                if (j < D) {
-                    v[q].re.x *= __ldg(&w0[j]);
-                    v[q].im.x *= __ldg(&w1[j]);
-                    v[q].re.y *= __ldg(&w2[j]);
-                    v[q].im.y *= __ldg(&w3[j]);
-                }
-            }
-        }
-        fft_regs<false, L, true, false>(v, buf, S.tw);
-        // every thread's staging reads are complete: the forward transform
-        // passed a barrier (N >= 32) or one is taken here (N = 16)
-        if constexpr (L < 5) __syncthreads();
-        prefetch(b + (int)gridDim.x);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const float2 hv = __ldg(&S.h[t + q * T]);
-            v[q].re = pmul(v[q].re, hv);
-            v[q].im = pmul(v[q].im, hv);
-        }
-        fft_regs<true, L, false, true>(v, buf, S.tw);
-        // v[q], q < 8, holds Q of the four rows at bin t + q T (bins past n_det
-        // are not zero: they are cleared below).  Every thread is past its last
-        // read of buf (the final pass of the inverse reads none; the one before
-        // ends with a barrier): publish the values so each thread can read its
-        // left neighbour's.  Layout (row 0, row 2, row 1, row 3).
-#pragma unroll
-        for (int q = 0; q < 8; ++q) put(buf, t + q * T, v[q]);
-        __syncthreads();
-        // the pair at p = t + q T is (Q[p-1], Q[p]) -> (mid, slope), Q zero
-        // outside [0, n_det); p runs to pitch/2 - 1 <= n_det + 3 (<= N/2 + 3)
-        OutT *r0 = static_cast<OutT *>(S.q) + (size_t)i0 * S.pitch;
-        const int P2 = S.pitch / 2;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            if (q * T >= P2) break;
-            const int p = t + q * T;
-            if (p < P2) {
-                float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), bv = a;
-                if (q < 8 && p < D) bv = make_float4(v[q].re.x, v[q].re.y, v[q].im.x, v[q].im.y);
-                if (p >= 1 && p - 1 < D) a = buf[pad16(p - 1)];
-                store_pair(r0, p, a.x, bv.x);
-                if (rows > 1) store_pair(r0 + S.pitch, p, a.z, bv.z);
-                if (rows > 2) store_pair(r0 + 2 * (size_t)S.pitch, p, a.y, bv.y);
-                if (rows > 3) store_pair(r0 + 3 * (size_t)S.pitch, p, a.w, bv.w);
-            }
-        }
-        __syncthreads();  // the next block's first exchange overwrites buf
+    int lo = 0, hi = P.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)blockIdx.x < P.s[mid].block_end) hi = mid; else lo = mid + 1;
     }
-    cp_async_wait_all();  // (an empty group: nothing is left in flight)
+    const FftSlice &S = P.s[lo];
+    const int blk = (int)blockIdx.x - (lo > 0 ? P.s[lo - 1].block_end : 0);
+    const int D = S.D, t = threadIdx.x;
+    const int i0 = 4 * blk;
+    const int rows = min(4, S.A - i0);  // 1..4 rows in this block
+    // rows i0, i0+1 -> transform 0 (re, im); rows i0+2, i0+3 -> transform 1;
+    // a row past the slice is never read
+    const float *p0 = S.sino + (size_t)i0 * S.ld;
+    const float *p1 = p0 + (rows > 1 ? S.ld : 0);
+    const float *p2 = p0 + (rows > 2 ? 2 * (size_t)S.ld : 0);
+    const float *p3 = p0 + (rows > 3 ? 3 * (size_t)S.ld : 0);
+    // n_det <= N/2: positions t + q T with q >= 8 are zero padding
+    C2 v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int j = t + q * T;
+        v[q].re = make_float2(0.0f, 0.0f);
+        v[q].im = make_float2(0.0f, 0.0f);
+        if (q < 8 && j < D) {
+            v[q].re.x = p0[j];
+            if (rows > 1) v[q].im.x = p1[j];
+            if (rows > 2) v[q].re.y = p2[j];
+            if (rows > 3) v[q].im.y = p3[j];
+        }
+    }
+    if (S.i0 > 0.0f) {
+        // intensities: convert after all loads are in flight (the padding stays zero)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (t + q * T < D) {
+                v[q].re.x = line_integral(v[q].re.x, S.i0, S.ln_i0);
+                if (rows > 1) v[q].im.x = line_integral(v[q].im.x, S.i0, S.ln_i0);
+                if (rows > 2) v[q].re.y = line_integral(v[q].re.y, S.i0, S.ln_i0);
+                if (rows > 3) v[q].im.y = line_integral(v[q].im.y, S.i0, S.ln_i0);
+            }
+        }
+    }
+    if (S.wt != nullptr) {
+        // per-element weights of the row (a cone-beam cosine weight), applied to the
+        // line integrals
+        const float *w0 = S.wt + (size_t)(i0 % S.wt_rows) * D;
+        const float *w1 = S.wt + (size_t)((i0 + 1) % S.wt_rows) * D;
+        const float *w2 = S.wt + (size_t)((i0 + 2) % S.wt_rows) * D;
+        const float *w3 = S.wt + (size_t)((i0 + 3) % S.wt_rows) * D;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = t + q * T;
+            if (j < D) {
+                v[q].re.x *= __ldg(&w0[j]);
+                v[q].im.x *= __ldg(&w1[j]);
+                v[q].re.y *= __ldg(&w2[j]);
+                v[q].im.y *= __ldg(&w3[j]);
+            }
+        }
+    }
+    fft_regs<false, L, true, false>(v, buf, S.tw);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float2 hv = __ldg(&S.h[t + q * T]);
+        v[q].re = pmul(v[q].re, hv);
+        v[q].im = pmul(v[q].im, hv);
+    }
+    fft_regs<true, L, false, true>(v, buf, S.tw);
+    // v[q], q < 8, holds Q of the four rows at bin t + q T (bins past n_det are
+    // not zero: they are cleared below).  Every thread is past its last read of
+    // buf (the final pass of the inverse reads none; the one before ends with
+    // a barrier): publish the values so each thread can read its left
+    // neighbour's.  Layout (row 0, row 2, row 1, row 3).
+#pragma unroll
+    for (int q = 0; q < 8; ++q) put(buf, t + q * T, v[q]);
+    __syncthreads();
+    // the pair at p = t + q T is (Q[p-1], Q[p]) -> (mid, slope), Q zero outside
+    // [0, n_det); p runs to pitch/2 - 1 <= n_det + 3 (<= N/2 + 3)
+    OutT *r0 = static_cast<OutT *>(S.q) + (size_t)i0 * S.pitch;
+    const int P2 = S.pitch / 2;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        if (q * T >= P2) break;
+        const int p = t + q * T;
+        if (p < P2) {
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), b = a;
+            if (q < 8 && p < D) b = make_float4(v[q].re.x, v[q].re.y, v[q].im.x, v[q].im.y);
+            if (p >= 1 && p - 1 < D) a = buf[pad16(p - 1)];
+            store_pair(r0, p, a.x, b.x);
+            if (rows > 1) store_pair(r0 + S.pitch, p, a.z, b.z);
+            if (rows > 2) store_pair(r0 + 2 * (size_t)S.pitch, p, a.y, b.y);
+            if (rows > 3) store_pair(r0 + 3 * (size_t)S.pitch, p, a.w, b.w);
+        }
+    }
 }
 
 int log2_of(int N)
@@ -645,20 +591,10 @@ template <typename OutT, int MAXS, int L>
 cudaError_t launch_one_len(const FftLaunch<MAXS> &P, int total, cudaStream_t s, bool prepare)
 {
     const size_t smem = filter_fft_smem_bytes(1 << L);
-    auto kern = filter_fft_kernel<OutT, MAXS, L>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    int per_sm = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (1 << L) / 16, smem);
+    cudaError_t e = cudaFuncSetAttribute(filter_fft_kernel<OutT, MAXS, L>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess || prepare) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = sms * (per_sm > 0 ? per_sm : 1);
-    if (grid > total) grid = total;
-    if (grid < 1) grid = 1;
-    kern<<<grid, (1 << L) / 16, smem, s>>>(P);
+    filter_fft_kernel<OutT, MAXS, L><<<total, (1 << L) / 16, smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -704,11 +640,7 @@ FftSlice fft_slice(const Plan &p, const float *sino, int ld, void *q)
 
 }  // namespace
 
-// exchange buffer (padded) and the staging of one row block (4 rows x N/2 positions)
-size_t filter_fft_smem_bytes(int N)
-{
-    return sizeof(float4) * (size_t)(N + N / 16) + sizeof(float) * 4 * (size_t)(N / 2);
-}
+size_t filter_fft_smem_bytes(int N) { return sizeof(float4) * (size_t)(N + N / 16); }
 
 cudaError_t launch_filter_fft(const Plan &p, const float *sino, int ld, void *q, cudaStream_t s)
 {
