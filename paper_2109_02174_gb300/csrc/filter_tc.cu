@@ -10,9 +10,9 @@
 // of one slice; one launch covers every slice that shares the plan:
 //   warp 0 (lane 0) issues tcgen05.mma, K-chunk after K-chunk (32 columns);
 //   warp 1 (lane 0) brings T_hi/T_lo tiles in with 2D TMA (128-byte swizzle);
-//   warps 2..9 bring the sinogram rows in by cp.async (4-byte copies, so any
-//   row stride works), three chunks ahead of the one they split, split them
-//   into tf32 hi/lo and store both in the same swizzled layout, then run the
+//   warps 2..9 load the sinogram rows with coalesced loads (the next chunk's
+//   values are in flight while the current ones are stored), split them into
+//   tf32 hi/lo and store both in the same swizzled layout, then run the
 //   epilogue: tcgen05.ld of the accumulators, (mid, slope) pairs of
 //   consecutive bins, stores to the filtered rows.
 // Tiles step by 126 output pairs and overlap by two columns so every pair's
@@ -48,12 +48,10 @@ constexpr int kBM = 128;      // output rows per tile (TMEM lanes)
 constexpr int kBN = 128;      // output bins per tile (TMEM columns)
 constexpr int kStep = 126;    // output pairs per tile
 constexpr int kBK = 32;       // fp32 elements per 128-byte swizzle row
-constexpr int kStages = 2;    // operand stages (A hi/lo, B hi/lo)
-constexpr int kRaw = 4;       // staged sinogram chunks in flight (cp.async)
+constexpr int kStages = 3;
 constexpr int kAcc = 4;       // accumulator slots (TMEM column blocks), ring
 constexpr int kTile = kBM * kBK * 4;          // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTile;        // A_hi, A_lo, B_hi, B_lo
-constexpr int kRawBytes = kBM * kBK * 4;      // one sinogram chunk, row-major
 constexpr int kLoadWarps = 8;  // warps 2..9: sinogram split, then epilogue
 constexpr int kThreads = 32 * (2 + kLoadWarps);
 constexpr int kRowsPerLoader = kBM / kLoadWarps;  // 16
@@ -201,15 +199,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t s0 = smem_addr(smem);
     const uint32_t base = (s0 + 1023u) & ~1023u;  // 1024-byte aligned: swizzle atoms
     unsigned char *bp = smem + (base - s0);
-    const uint32_t raw0 = base + kStages * kStageBytes;            // [kRaw] sinogram chunks
-    const uint32_t bar_full_a = raw0 + kRaw * kRawBytes;           // [kStages], 256 arrivals
+    const uint32_t bar_full_a = base + kStages * kStageBytes;      // [kStages], 128 arrivals
     const uint32_t bar_full_b = bar_full_a + 8 * kStages;          // [kStages], TMA bytes
     const uint32_t bar_empty = bar_full_b + 8 * kStages;           // [kStages], MMA commit
     const uint32_t bar_acc_full = bar_empty + 8 * kStages;         // [kAcc], MMA commit
     const uint32_t bar_acc_free = bar_acc_full + 8 * kAcc;         // [kAcc], epilogue warps
     uint32_t *tmem_slot =
-        reinterpret_cast<uint32_t *>(bp + kStages * kStageBytes + kRaw * kRawBytes +
-                                     8 * (3 * kStages + 2 * kAcc));
+        reinterpret_cast<uint32_t *>(bp + kStages * kStageBytes + 8 * (3 * kStages + 2 * kAcc));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -350,42 +346,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive_cta(bar_acc_free + 8 * blk);
             return true;
         };
-        // The sinogram chunks come in by cp.async, kRaw - 1 chunks ahead: lane
-        // = column k of the chunk, rows 16 cw .. 16 cw + 15 (zero outside the
-        // slice and the detector).  Each thread reads back only its own copies.
-        const unsigned char *raw_ptr = bp + kStages * kStageBytes;
-        auto issue_chunk = [&](int kc) {
-            if (kc < args.nk) {
-                const int k = kc * kBK + lane;
-                const uint32_t dst = raw0 + (uint32_t)((kc % kRaw) * kRawBytes) +
-                                     (uint32_t)((cw * kRowsPerLoader * kBK + lane) * 4);
+        float cur[kRowsPerLoader], nxt[kRowsPerLoader];
+        auto load_chunk = [&](int kc, float (&v)[kRowsPerLoader]) {
+            const int k = kc * kBK + lane;
 #pragma unroll
-                for (int i = 0; i < kRowsPerLoader; ++i) {
-                    const int m = m0 + cw * kRowsPerLoader + i;
-                    const bool in = m < args.A && k < args.D;
-                    const float *src = in ? sino + (size_t)m * ld + k : sino;
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                                     dst + (uint32_t)(i * kBK * 4)),
-                                 "l"(src), "r"(in ? 4 : 0)
-                                 : "memory");
-                }
+            for (int i = 0; i < kRowsPerLoader; ++i) {
+                const int m = m0 + cw * kRowsPerLoader + i;
+                v[i] = (m < args.A && k < args.D) ? __ldg(&sino[(size_t)m * ld + k]) : 0.0f;
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
         };
-#pragma unroll
-        for (int j = 0; j < kRaw - 1; ++j) issue_chunk(j);
         bool ok = true;
+        if (args.nk > 0) load_chunk(0, cur);
         for (int kc = 0; kc < args.nk && ok; ++kc) {
             const int s = kc % kStages;
             const uint32_t use = (uint32_t)(kc / kStages);
-            // refill the slot this thread read last iteration, then wait for chunk kc
-            issue_chunk(kc + kRaw - 1);
-            asm volatile("cp.async.wait_group %0;" ::"n"(kRaw - 1) : "memory");
-            float cur[kRowsPerLoader];
-            const float *rp = reinterpret_cast<const float *>(raw_ptr + (kc % kRaw) * kRawBytes) +
-                              cw * kRowsPerLoader * kBK + lane;
-#pragma unroll
-            for (int i = 0; i < kRowsPerLoader; ++i) cur[i] = rp[i * kBK];
+            if (kc + 1 < args.nk) load_chunk(kc + 1, nxt);
             if (*abort_flag) {
                 ok = false;
                 break;
@@ -401,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < kRowsPerLoader; ++i) {
                 const int r = cw * kRowsPerLoader + i;
                 float x = cur[i];
-                // intensities: converted here, after their copies landed
+                // intensities: converted here, a chunk after their loads were issued
                 if constexpr (INTENSITY)
                     if (m0 + r < args.A && kc * kBK + lane < args.D)
                         x = line_integral(x, args.i0, args.ln_i0);
@@ -416,9 +391,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async_smem();  // generic-proxy stores -> tensor-core reads
             // (tests only: the first CTA may withhold one stage's arrival)
             if (kc != withhold) mbar_arrive_cta(bar_full_a + 8 * s);
+#pragma unroll
+            for (int i = 0; i < kRowsPerLoader; ++i) cur[i] = nxt[i];
             if (kc >= 1) ok = drain(kc - 1);  // the previous chunk's MMAs are (nearly) done
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");  // no copy in flight past here
         if (ok && args.nk > 0) ok = drain(args.nk - 1);
         if (ok && !*abort_flag) {
             const int m = m0 + quarter * 32 + lane;
@@ -448,8 +424,7 @@ cudaError_t set_wait_hook_filter_tc(const WaitHook &h) { return write_wait_hook(
 
 size_t filter_tc_smem_bytes()
 {
-    return (size_t)kStages * kStageBytes + (size_t)kRaw * kRawBytes + 8 * (3 * kStages + 2 * kAcc) +
-           16 + 1024;
+    return (size_t)kStages * kStageBytes + 8 * (3 * kStages + 2 * kAcc) + 16 + 1024;
 }
 
 cudaError_t launch_filter_tc_many(const Plan &p, const float *const *sinos, const int *lds,
