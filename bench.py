@@ -39,12 +39,11 @@ FILTER_PATHS = {"auto": 0, "tc": 1, "fft": 2, "direct": 3}
 # wavefronts, so at most 16 updates per clock per SM.
 SMEM_UPDATES_PER_CLK_SM = 16
 # DRAM bytes (read + write) of one backprojection launch, measured by ncu on
-# the launch this script times for the two shapes the tuner picks between
+# the launch this script times for the shape the tuner picks
 # (profiles/bp_persistent_kernel_batch64_512x720x725.md),
 # keyed by (geometry, slices, tile_x, tile_y, angle_chunk); reported only when
 # the tuned launch is that one, null otherwise.
-BP_TRAFFIC = {("512x720x725", 64, 32, 32, 32): 247808768 + 53537792,
-              ("512x720x725", 64, 32, 64, 32): 250698496 + 54441472}
+BP_TRAFFIC = {("512x720x725", 64, 32, 32, 32): 247914240 + 55627520}
 ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
