@@ -45,6 +45,7 @@
 // in flight when the CTA exits.  For tests, the first CTA can withhold one
 // stage's arrival (no TMA issued for it), which makes those waits run out.
 #include <cstring>
+#include <type_traits>
 
 #include "backproject.cuh"
 #include "ptx.cuh"
@@ -279,9 +280,11 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 __syncwarp();
                 // (tests only: a withheld stage gets neither its arrival nor its loads)
                 const bool fill = (int)it != withhold;
+                // rows of the item: a single slice in a two-slice launch stages one
+                const int rows = (G == 2 && !PP && S.image2 == nullptr) ? 1 : G;
                 if (lane == 0 && fill) {
                     const uint32_t bar = full0 + 8u * s;
-                    mbar_arrive_expect_tx(bar, (uint32_t)(G * na * S.wp * TR::kBytes));
+                    mbar_arrive_expect_tx(bar, (uint32_t)(rows * na * S.wp * TR::kBytes));
                 }
                 __syncwarp();
                 // each lane issues its own angle's load(s) (x in elements of PairT);
@@ -289,6 +292,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                 if (lane < na && fill) {
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
+                        if (g >= rows) break;
                         // two slices: the same window of each slice's rows; point
                         // pairs: the partner tile's window of the one slice
                         const int xg = (PP && g) ? pbb : pb;
@@ -344,11 +348,16 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
 #pragma unroll
         for (int j = 0; j < (KAHAN ? PPT : 1); ++j) cmp[j] = 0.0f;
 
+        // The item's angle chunks; GC = rows of the item actually staged (a
+        // two-slice launch also carries single slices: their second row is
+        // absent).  false: a wait ran out.
+        auto chunks = [&](auto gcv) -> bool {
+        constexpr int GC = decltype(gcv)::value;
         for (int cc = 0; cc < nch; ++cc, ++it) {
             const int s = (int)(it % NSTAGE);
             if ((cc > 0 || !dyn) && !wait_full(it)) {
                 if (lane == 0) *reinterpret_cast<volatile int *>(P.status) = FBP_ERR_TIMEOUT;
-                return;
+                return false;
             }
             const int na = min(CH, S.A - cc * CH);
             const uint32_t stage_addr = base_addr + (uint32_t)(s * L.stage);
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     const uint32_t o0 = (__float_as_uint(t.x) << TR::kShift) + cb;
                     const uint32_t o1 = (__float_as_uint(t.y) << TR::kShift) + cb;
 #pragma unroll
-                    for (int g = 0; g < G; ++g) {
+                    for (int g = 0; g < GC; ++g) {
                         uint32_t a0, a1;
                         if constexpr (PP) {
                             a0 = g ? cbb - (__float_as_uint(t.x) << TR::kShift) : o0;
@@ -416,6 +425,13 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8u * s);
         }
+        return true;
+        };
+        // single slice in a two-slice launch: its own loop, no second row
+        const bool solo = G == 2 && !PP && S.image2 == nullptr;
+        const bool ok = solo ? chunks(std::integral_constant<int, 1>())
+                             : chunks(std::integral_constant<int, G>());
+        if (!ok) return;
 
         if constexpr (PP) {
             // tile A and, mirrored through the image centre, its partner
@@ -433,6 +449,7 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     float *img = g ? S.image2 : S.image;
+                    if (img == nullptr) break;  // a single slice of a two-slice launch
 #pragma unroll
                     for (int j = 0; j < PPT; ++j) {
                         const int row = ty * TY + ly0 + 4 * j;

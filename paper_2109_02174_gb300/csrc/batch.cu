@@ -202,39 +202,50 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
         } else {
             singles = members;
         }
-        for (int group = 2; group >= 1; --group) {
-            const int count = group == 2 ? (int)pairs.size() : (int)singles.size();
-            for (int b = 0; b < count; b += kBpMaxSlices) {
-                const int cnt = std::min(kBpMaxSlices, count - b);
-                std::memset(L.get(), 0, sizeof(*L));
-                int acc = 0;
-                for (int m = 0; m < cnt; ++m) {
-                    const int i = group == 2 ? pairs[(size_t)(b + m)].first : singles[(size_t)(b + m)];
-                    const Plan &p = *plans[i];
-                    if (!encode_pairs_map(p, io[i].workspace, &L->maps[group * m]))
+        // Work-list entries: (slice, partner or -1).  Plain-sum configurations
+        // put the pairs and the odd slices out into one two-slice launch (a
+        // single slice stages one row per angle there), most angles first;
+        // Kahan and point-pair configurations launch single-slice items.
+        const bool two = !cfg.kahan && !cfg.point_pairs;
+        std::vector<std::pair<int, int>> entries = pairs;
+        for (int i : singles) entries.push_back(std::make_pair(i, -1));
+        std::stable_sort(entries.begin(), entries.end(),
+                         [&](const std::pair<int, int> &a, const std::pair<int, int> &c) {
+                             return plans[a.first]->A > plans[c.first]->A;
+                         });
+        const int group = two ? 2 : 1;
+        const int count = (int)entries.size();
+        for (int b = 0; b < count; b += kBpMaxSlices) {
+            const int cnt = std::min(kBpMaxSlices, count - b);
+            std::memset(L.get(), 0, sizeof(*L));
+            int acc = 0;
+            for (int m = 0; m < cnt; ++m) {
+                const int i = entries[(size_t)(b + m)].first;
+                const int j = entries[(size_t)(b + m)].second;
+                const Plan &p = *plans[i];
+                if (!encode_pairs_map(p, io[i].workspace, &L->maps[group * m]))
+                    return cudaErrorInvalidValue;
+                L->slices[m] = slice_desc(p, static_cast<float *>(io[i].image));
+                if (j >= 0) {
+                    if (!encode_pairs_map(*plans[j], io[j].workspace, &L->maps[2 * m + 1]))
                         return cudaErrorInvalidValue;
-                    L->slices[m] = slice_desc(p, static_cast<float *>(io[i].image));
-                    if (group == 2) {
-                        const int j = pairs[(size_t)(b + m)].second;
-                        if (!encode_pairs_map(*plans[j], io[j].workspace, &L->maps[2 * m + 1]))
-                            return cudaErrorInvalidValue;
-                        L->slices[m].image2 = static_cast<float *>(io[j].image);
-                    }
-                    acc += items_of(p);
-                    L->tile_end[m] = acc;
-                    L->wp_max = std::max(L->wp_max, p.bp_wp);
+                    L->slices[m].image2 = static_cast<float *>(io[j].image);
                 }
-                L->n_slices = cnt;
-                L->n_items = acc;
-                L->status = status;
-                L->sched = (sched != nullptr && launches < n_sched) ? sched + 2 * launches : nullptr;
-                ++launches;
-                BpConfig c = cfg;
-                c.group = group;
-                const bool on_side = forked && group == 1;
-                cudaError_t e = launch_backproject_batch(*L, c, 0, on_side ? fork->side : s);
-                if (e != cudaSuccess) return e;
+                acc += items_of(p);
+                L->tile_end[m] = acc;
+                L->wp_max = std::max(L->wp_max, p.bp_wp);
             }
+            L->n_slices = cnt;
+            L->n_items = acc;
+            L->status = status;
+            L->sched = (sched != nullptr && launches < n_sched) ? sched + 2 * launches : nullptr;
+            ++launches;
+            BpConfig c = cfg;
+            c.group = group;
+            // single-slice launches run beside the two-slice ones
+            const bool on_side = forked && group == 1;
+            cudaError_t e = launch_backproject_batch(*L, c, 0, on_side ? fork->side : s);
+            if (e != cudaSuccess) return e;
         }
     }
     if (forked) {
@@ -335,7 +346,8 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
     }
 
     // Capture the whole batch once into a graph on a private stream, the
-    // single-slice backprojection launches on a forked branch.
+    // single-slice-item backprojection launches (Kahan and point-pair
+    // configurations) on a forked branch.
     cudaStream_t cs = nullptr;
     BpFork fork = {nullptr, nullptr, nullptr};
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);

@@ -296,6 +296,33 @@ def test_kernel_count_of_a_same_plan_batch(fbp):
     assert batch.kernel_count == 2
 
 
+def test_odd_slices_ride_in_the_two_slice_launch(fbp):
+    """Five slices of one plan and one of another plan with the same kernel
+    configuration: two pairs and two single slices, all in one two-slice
+    backprojection launch (a single slice stages one row per angle).  One
+    filter launch plus one backprojection launch; every image equals its
+    alone result bit for bit, over images first filled with NaN."""
+    import torch
+    n, A = 96, 60
+    D = synthetic.det_for(n)
+    a = fbp.Plan(n, A, D, filter_path=2, tile_x=8, tile_y=32)
+    b = fbp.Plan(128, 90, synthetic.det_for(128), filter_path=2, tile_x=8, tile_y=32)
+    plans = [a, a, b, a, a, a]
+    specs = [synthetic.SliceSpec(p.n_pix, p.n_angles, p.n_det, 5, seed=1200 + i)
+             for i, p in enumerate(plans)]
+    sinos = [_sino(s) for s in specs]
+    batch = fbp.Batch(plans, sinos)
+    assert batch.kernel_count == 2
+    for rep in range(2):
+        for im in batch.images:
+            im.fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        batch.status()
+        for p, s, im in zip(plans, sinos, batch.images):
+            assert np.array_equal(im.cpu().numpy(), _alone(fbp, p, s)), rep
+
+
 def test_point_pair_plans_in_batches_bitwise(fbp):
     """Slices of point-pair plans (a tile and its mirror image per work item)
     batched with other plans: each image equals its alone result bit for bit,
