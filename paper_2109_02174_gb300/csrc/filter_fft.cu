@@ -82,30 +82,21 @@ __device__ __forceinline__ Tw tmul(const Tw &a, const Tw &b)
     return w;
 }
 
-// Plan twiddle t, exp(-2 pi i t / N) (forward) or its conjugate (inverse).
-template <bool INV>
-__device__ __forceinline__ Tw tw_load(const float4 *__restrict__ tw, int t)
-{
-    const float4 v = __ldg(&tw[t]);
-    const float2 s = make_float2(v.z, v.w);
-    const float2 n = pneg(s);
-    Tw w;
-    w.r = make_float2(v.x, v.y);
-    w.s = INV ? n : s;
-    w.n = INV ? s : n;
-    return w;
-}
-
-// tw_load through a volatile load: the last pass's twiddles stay after the
-// preceding exchange (hoisted above it, fourteen of them would be live across
-// it and spill registers).
-template <bool INV>
-__device__ __forceinline__ Tw tw_load_late(const float4 *__restrict__ tw, int t)
+// A table entry through a volatile load, so it is issued where it is written.
+__device__ __forceinline__ float4 tw_raw(const float4 *__restrict__ tw, int t)
 {
     float4 v;
     asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                  : "l"(tw + t));
+    return v;
+}
+
+// Plan twiddle t, exp(-2 pi i t / N) (forward) or its conjugate (inverse),
+// from its table entry (cos, cos, sin, sin).
+template <bool INV>
+__device__ __forceinline__ Tw tw_from_raw(const float4 &v)
+{
     const float2 s = make_float2(v.z, v.w);
     const float2 n = pneg(s);
     Tw w;
@@ -293,6 +284,16 @@ __device__ __forceinline__ void dft8_lo4(C2 (&a)[8])
     for (int m = 0; m < 4; ++m) a[m] = x[m];
 }
 
+// Last pass of radix R: element m + S (16/R) (butterfly j = t + m T) times
+// w^{S j} = w^{S t} exp(-+ 2 pi i S m / 16), from the one twiddle w^{S t}.
+template <bool INV, int R, int S, int M>
+__device__ __forceinline__ void last_scale(C2 (&v)[16], const Tw &w)
+{
+    constexpr int idx = M + S * (16 / R);
+    v[idx] = twiddle16<INV, (S * M) % 16>(cmul(v[idx], w));
+    if constexpr (M + 1 < 16 / R) last_scale<INV, R, S, M + 1>(v, w);
+}
+
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ void put(float4 *buf, int i, const C2 &a)
@@ -320,14 +321,37 @@ __device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 
     constexpr int NP = L >> 2;   // radix-16 passes
     constexpr int REM = L & 3;   // bits of the last pass (radix 2^REM), 0: none
     const int t = threadIdx.x;
+    int np = NP;
+    asm volatile("" : "+r"(np));
+    // the next pass's table entries, loaded during the exchange before it
+    // (after the stores, before the barrier: the data registers are free)
+    float4 x1, x2, x4, x8;
+    auto preload = [&](int pn) {
+        if (pn < np) {
+            const int log2ns = 4 * pn;
+            const int k = t & ((1 << log2ns) - 1);
+            const int i1 = k << (L - 4 - log2ns);  // k N / (16 ns)
+            x1 = tw_raw(tw, i1);
+            x2 = tw_raw(tw, 2 * i1);
+            x4 = tw_raw(tw, 4 * i1);
+            x8 = tw_raw(tw, 8 * i1);
+        } else {
+            // last pass: w^{t}, w^{2t}, w^{4t} (the other butterflies' and
+            // powers' twiddles follow from these)
+            if constexpr (REM >= 1) x1 = tw_raw(tw, t);
+            if constexpr (REM >= 2) x2 = tw_raw(tw, 2 * t);
+            if constexpr (REM == 3) x4 = tw_raw(tw, 4 * t);
+        }
+    };
     // the exchange after a radix-16 pass: write positions o + m ns from wb with
     // stride ws (padded), read t + q T
-    auto exchange = [&](int wb, int ws) {
+    auto exchange = [&](int wb, int ws, int pn) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const C2 &a = v[m];
             buf[wb + m * ws] = make_float4(a.re.x, a.re.y, a.im.x, a.im.y);
         }
+        preload(pn);
         __syncthreads();
         if constexpr (T >= 16) {
             const int rb = t + (t >> 4);
@@ -348,21 +372,18 @@ __device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 
     else if constexpr (FIRST_HALF_ZERO) dft16p<INV, true, false>(v);
     else if constexpr (LAST0 && LAST_LO8) dft16p<INV, false, true>(v);
     else dft16<INV>(v);
-    if constexpr (!LAST0) exchange(17 * t, 1);
+    if constexpr (!LAST0) exchange(17 * t, 1, 1);
     // passes 1 .. NP-1 (ns = 16^p), kept as a loop whose trip count the
     // compiler cannot see: straight-line (one middle pass, N = 2^9 .. 2^11), its
     // schedule overlaps the passes and spills registers
-    int np = NP;
-    asm volatile("" : "+r"(np));
 #pragma unroll 1
     for (int p = 1; p < np; ++p) {
         const int log2ns = 4 * p;
         const int ns = 1 << log2ns;
         const bool last = REM == 0 && p == NP - 1;
         const int k = t & (ns - 1);
-        const int i1 = k << (L - 4 - log2ns);  // k N / (16 ns)
-        const Tw w1 = tw_load<INV>(tw, i1), w2 = tw_load<INV>(tw, 2 * i1);
-        const Tw w4 = tw_load<INV>(tw, 4 * i1), w8 = tw_load<INV>(tw, 8 * i1);
+        const Tw w1 = tw_from_raw<INV>(x1), w2 = tw_from_raw<INV>(x2);
+        const Tw w4 = tw_from_raw<INV>(x4), w8 = tw_from_raw<INV>(x8);
         const Tw w3 = tmul(w1, w2);
         v[1] = cmul(v[1], w1);
         v[2] = cmul(v[2], w2);
@@ -388,7 +409,7 @@ __device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 
         if (!last) {
             // outputs o + m ns, o = 16 (t - k) + k; padded pad16(o) + m (ns + ns/16)
             const int o = ((t - k) << 4) + k;
-            exchange(pad16(o), ns + (ns >> 4));
+            exchange(pad16(o), ns + (ns >> 4), p + 1);
         }
     }
     if constexpr (REM == 0) return;
@@ -396,12 +417,23 @@ __device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 
     // takes positions j + s N/R = t + (m + s 16/R) T, twiddles exp(-+ 2 pi i s j / N);
     // with LAST_LO8 only the outputs at q = m + s 16/R < 8 are formed
     if constexpr (REM == 3) {
+        {
+            const Tw w1 = tw_from_raw<INV>(x1), w2 = tw_from_raw<INV>(x2);
+            const Tw w4 = tw_from_raw<INV>(x4);
+            last_scale<INV, 8, 1, 0>(v, w1);
+            last_scale<INV, 8, 2, 0>(v, w2);
+            last_scale<INV, 8, 4, 0>(v, w4);
+            last_scale<INV, 8, 5, 0>(v, tmul(w4, w1));
+            last_scale<INV, 8, 6, 0>(v, tmul(w4, w2));
+            const Tw w3 = tmul(w1, w2);
+            last_scale<INV, 8, 3, 0>(v, w3);
+            last_scale<INV, 8, 7, 0>(v, tmul(w4, w3));
+        }
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
-            const int j = t + m * T;
             C2 a[8];
 #pragma unroll
-            for (int s = 0; s < 8; ++s) a[s] = s ? cmul(v[m + 2 * s], tw_load_late<INV>(tw, s * j)) : v[m];
+            for (int s = 0; s < 8; ++s) a[s] = v[m + 2 * s];
             if constexpr (LAST_LO8) {
                 dft8_lo4<INV>(a);
 #pragma unroll
@@ -413,12 +445,15 @@ __device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 
             }
         }
     } else if constexpr (REM == 2) {
+        {
+            const Tw w1 = tw_from_raw<INV>(x1), w2 = tw_from_raw<INV>(x2);
+            last_scale<INV, 4, 1, 0>(v, w1);
+            last_scale<INV, 4, 2, 0>(v, w2);
+            last_scale<INV, 4, 3, 0>(v, tmul(w1, w2));
+        }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const int j = t + m * T;
-            C2 a1 = cmul(v[m + 4], tw_load_late<INV>(tw, j));
-            C2 a2 = cmul(v[m + 8], tw_load_late<INV>(tw, 2 * j));
-            C2 a3 = cmul(v[m + 12], tw_load_late<INV>(tw, 3 * j));
+            C2 a1 = v[m + 4], a2 = v[m + 8], a3 = v[m + 12];
             if constexpr (LAST_LO8) {
                 dft4_out01<INV>(v[m], a1, a2, a3);
                 v[m + 4] = a1;
@@ -430,13 +465,13 @@ __device__ __forceinline__ void fft_regs(C2 (&v)[16], float4 *buf, const float4 
             }
         }
     } else {
+        last_scale<INV, 2, 1, 0>(v, tw_from_raw<INV>(x1));
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int j = t + m * T;
-            C2 a1 = cmul(v[m + 8], tw_load_late<INV>(tw, j));
             if constexpr (LAST_LO8) {
-                v[m] = cadd(v[m], a1);
+                v[m] = cadd(v[m], v[m + 8]);
             } else {
+                C2 a1 = v[m + 8];
                 dft2<INV>(v[m], a1);
                 v[m + 8] = a1;
             }
