@@ -851,6 +851,31 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = _timed(lambda: full.run_host(h_sino, h_img), e2e_steps, stream)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
+    # ---- the same batch with FP16-stored pairs (the precision variant; its
+    # own tuned plan): the whole step and its backprojection launch alone
+    fp16 = None
+    if rank == 0 and not args.no_configs:
+        plan16 = fbp.Plan(spec0.n_pix, spec0.n_angles, spec0.n_det, filter=spec0.filter,
+                          autotune=True, batch_hint=min(S, 64), q_storage=2)
+        works16 = [plan16.empty_workspace() for _ in range(S)]
+        full16 = fbp.Batch([plan16] * S, sinos, images, works16)
+        bp16 = fbp.Batch([plan16] * S, sinos, images, works16, parts=fbp.FBP_BATCH_BACKPROJECT)
+        full16.launch()
+        ms16 = _timed(full16.launch, max(args.steps // 2, 5), stream) / max(args.steps // 2, 5)
+        bp16.launch()
+        _, bp16_ms = _timed(bp16.launch, max(args.steps // 4, 5), stream, per_launch=True)
+        full16.status()
+        t16 = plan16.tuning or {}
+        fp16 = {"slices_per_s": S / (ms16 / 1e3), "ms_per_step": ms16,
+                "backprojection_gupdates_per_s":
+                    S * spec0.updates / (sum(bp16_ms) / len(bp16_ms) / 1e3) / 1e9,
+                "tile": [t16.get("tile_x"), t16.get("tile_y"), t16.get("angle_chunk")],
+                "what": "the headline batch with (mid, slope) pairs stored in FP16 and "
+                        "summed in FP32 (mixed-precision FMA); error stated, no bar"}
+        full16.close()
+        bp16.close()
+        del works16
+
     if rank != 0:
         return 0
     total_slices = S * args.steps * world
@@ -872,6 +897,7 @@ def run_ours(args, rank, world, local_rank):
         "plain_path": {"value": S * plain_steps / (plain_ms / 1e3), "unit": "slices/s",
                        "what": "one fbp_reconstruct call per slice, same slices and stream"},
         "filter_ms_per_step": filt_ms,
+        "fp16_pairs_batched": fp16,
         "config": {"workload": WORKLOAD_NAME, "slices_per_step": S * world,
                    "path": ("batched: one captured graph per step (%s + one persistent "
                             "backprojection launch over all slices' tiles)" %

@@ -72,6 +72,30 @@ __device__ __forceinline__ float2 lds_h2_as_f2(uint32_t addr)
     return __half22float2(v);
 }
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t h;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(h) : "r"(addr));
+    return h;
+}
+
+// acc + mid + w slope for an FP16 (mid, slope) pair (mid in the low half),
+// in FP32 with the FP16 operands taken as they are (no conversion); the
+// weight is the low (LO) or high half of the packed f16 pair w2.
+template <bool LO>
+__device__ __forceinline__ float acc_pair_f16(float acc, uint32_t pair, uint32_t w2)
+{
+    if constexpr (LO)
+        asm("{\n\t.reg .b16 m, s, wl, wh;\n\tmov.b32 {m, s}, %1;\n\tmov.b32 {wl, wh}, %2;\n\t"
+            "add.rn.f32.f16 %0, m, %0;\n\tfma.rn.f32.f16 %0, wl, s, %0;\n\t}"
+            : "+f"(acc) : "r"(pair), "r"(w2));
+    else
+        asm("{\n\t.reg .b16 m, s, wl, wh;\n\tmov.b32 {m, s}, %1;\n\tmov.b32 {wl, wh}, %2;\n\t"
+            "add.rn.f32.f16 %0, m, %0;\n\tfma.rn.f32.f16 %0, wh, s, %0;\n\t}"
+            : "+f"(acc) : "r"(pair), "r"(w2));
+    return acc;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -382,6 +406,10 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     const float2 w = __ffma2_rn(kf, kNeg1, v);
                     const uint32_t o0 = (__float_as_uint(t.x) << TR::kShift) + cb;
                     const uint32_t o1 = (__float_as_uint(t.y) << TR::kShift) + cb;
+                    // FP16 pairs: the two fractions as an f16 pair (low: w.x)
+                    uint32_t w16 = 0;
+                    if constexpr (TR::kBytes == 4 && !KAHAN)
+                        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(w16) : "f"(w.y), "f"(w.x));
 #pragma unroll
                     for (int g = 0; g < GC; ++g) {
                         uint32_t a0, a1;
@@ -392,6 +420,14 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                             const uint32_t go = (uint32_t)(g * CH * L.row);
                             a0 = o0 + go;
                             a1 = o1 + go;
+                        }
+                        if constexpr (TR::kBytes == 4 && !KAHAN) {
+                            // the partner's weight is -w: flip both sign bits
+                            const uint32_t wg = (PP && g) ? (w16 ^ 0x80008000u) : w16;
+                            acc[g][2 * jj] = acc_pair_f16<true>(acc[g][2 * jj], lds_u32(a0), wg);
+                            acc[g][2 * jj + 1] =
+                                acc_pair_f16<false>(acc[g][2 * jj + 1], lds_u32(a1), wg);
+                            continue;
                         }
                         float2 q0, q1;
                         if constexpr (TR::kBytes == 8) {

@@ -254,8 +254,10 @@ def test_kahan_accumulation_meets_fp32_bars(fbp):
 
 
 def test_fp16_pairs_error_is_stated(fbp):
-    """FP16-stored (mid, slope) pairs: no bar from the spec; the error is reported
-    and must stay in the range half precision allows (~1e-3 of max|f|)."""
+    """FP16-stored (mid, slope) pairs: no bar from the spec; the error is reported.
+    The bound below is a regression guard, about six times the measured error
+    (max 7e-5, RMSE 1e-5): the storage rounding (2^-11 of each stored value) and
+    the FP16 weight fed to the mixed-precision FMA, averaged over 180 angles."""
     import torch
     spec = synthetic.cfg_plain()
     th = synthetic.default_angles(spec.n_angles)
@@ -267,7 +269,7 @@ def test_fp16_pairs_error_is_stated(fbp):
     ref = oracle.fbp(sino32.astype(np.float64), th, 1.0, 0, spec.n_pix, nthreads=NTHREADS)
     e_max, e_rms = errors(got, ref)
     print(f"fp16 pairs: max {e_max:.3e} rmse {e_rms:.3e} of max|f|")
-    assert e_max < 5e-3 and e_rms < 1e-3
+    assert e_max < 5e-4 and e_rms < 1e-4
 
 
 # ---------------------------------------------------------------- FP64 path
@@ -504,7 +506,7 @@ def test_point_pairs_match_oracle(fbp, geom):
     ref = oracle.fbp(sino32.astype(np.float64), th, tau, 0, n, nthreads=NTHREADS)
     if g.get("q_storage") == 2:
         e_max, e_rms = errors(imgs[1], ref)
-        assert e_max < 5e-3 and e_rms < 1e-3
+        assert e_max < 5e-4 and e_rms < 1e-4
         e2 = errors(imgs[-1], ref)
         assert abs(e_max - e2[0]) < 0.5 * e2[0] + 1e-6
     else:

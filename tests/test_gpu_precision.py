@@ -2,7 +2,7 @@
 40 ellipses).  Every combination of {FP32, FP16}-stored pairs x {plain, Kahan}
 accumulation x {tensor-core, FFT} filter is compared with the FP64 oracle's
 image at every pixel; the error of each is reported, the FP32 ones must meet
-the bars (FP16 pairs have no bar)."""
+the bars (FP16 pairs have no bar, only a regression guard)."""
 import json
 import os
 
@@ -55,4 +55,6 @@ def test_large_variant_error(fbp, large_reference, q_storage, accumulate, path):
     if q_storage == 0:
         assert e_max <= MAX_REL and e_rms <= RMSE_REL, line
     else:
-        assert e_max < 2e-2, line  # half precision: stated, loose sanity bound only
+        # half precision: no bar; a regression guard about 20 times the
+        # measured error (max 2.4e-5, RMSE 3.3e-6)
+        assert e_max < 5e-4 and e_rms < 1e-4, line
