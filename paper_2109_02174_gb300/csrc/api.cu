@@ -483,7 +483,10 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     // microseconds, without / with pairs: 512^2 x 720 at 32 x 32: 72.3 / 84.6;
     // 768^2 x 1440 at 32 x 64: 240 / 214, at 32 x 32: 249 / 216;
     // 1024^2 x 1440: 469 / 418, 484 / 425; 1536^2 x 1024: 664 / 591,
-    // 687 / 570; 2048^2 x 2048: 2293 / 2040, 2380 / 1934.
+    // 687 / 570; 2048^2 x 2048: 2293 / 2040, 2380 / 1934.  FP16 pairs keep
+    // 32 x 64 with point pairs where that tiling allows them (2048^2 x 2048,
+    // backprojection alone: 1.868 ms on 32 x 64, 1.982 on 32 x 32; FP32 pairs
+    // 2.039 and 1.932).
     auto pairs_fit = [&](int tx, int ty) {
         const int gx = n_pix / tx, gy = n_pix / ty;
         return o.dtype == FBP_F32 && o.accumulate == FBP_ACC_PLAIN && n_pix % tx == 0 &&
@@ -492,9 +495,11 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     const long tiles_big = (long)((n_pix + 31) / 32) * (long)((n_pix + 63) / 64);
     const bool pairs_auto = o.point_pairs == 0 && 4 * tiles_big >= 7L * sms;
     if (pick >= 0 && !largest && !o.tile_x && !o.tile_y && o.point_pairs >= 0 &&
-        (pairs_auto || o.point_pairs > 0) && pairs_fit(32, 32) &&
-        window_pairs(trig, 32, 32, align) <= 128)
-        pick = 1;  // 32 x 32
+        (pairs_auto || o.point_pairs > 0)) {
+        const bool keep_wide = o.q_storage == FBP_F16 && pick == 0 && pairs_fit(32, 64);
+        if (!keep_wide && pairs_fit(32, 32) && window_pairs(trig, 32, 32, align) <= 128)
+            pick = 1;  // 32 x 32
+    }
     if (pick < 0) {
         delete p;
         set_error("fbp_plan: no backprojection tile fits the detector window (det_spacing %.3g, "

@@ -129,8 +129,8 @@ def test_default_tile_rule(fbp):
 
 def test_default_plan_of_a_large_slice_takes_point_pairs(fbp):
     """From n_pix > 704 (on 152 SMs) the automatic tile is 32 x 32 with
-    point-symmetric tile pairs; a named tile keeps single-tile items unless
-    point_pairs = 1 asks for them."""
+    point-symmetric tile pairs (32 x 64 for FP16 pairs); a named tile keeps
+    single-tile items unless point_pairs = 1 asks for them."""
     import torch
     n, A = 768, 90
     D = synthetic.det_for(n)
@@ -149,3 +149,9 @@ def test_default_plan_of_a_large_slice_takes_point_pairs(fbp):
         assert np.array_equal(img(), paired)
     assert np.array_equal(img(tile_x=32, tile_y=32), single)
     assert np.array_equal(img(point_pairs=-1), img(tile_x=32, tile_y=64, point_pairs=-1))
+    # FP16 pairs keep the 32 x 64 tile under point pairs
+    if 4 * 24 * 12 >= 7 * sms:
+        assert np.array_equal(img(q_storage=2),
+                              img(q_storage=2, tile_x=32, tile_y=64, point_pairs=1))
+        assert not np.array_equal(img(q_storage=2),
+                                  img(q_storage=2, tile_x=32, tile_y=32, point_pairs=1))
