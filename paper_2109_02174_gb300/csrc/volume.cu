@@ -140,9 +140,6 @@ fbp_status fbp_volume_from_slices(const void *const *slices, int n_slices, const
         for (int j = G.cnt; j < kGroup; ++j) G.wa[j] = G.wb[j] = 0.0f;
         groups.push_back(G);
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int n_groups = (int)groups.size();
     for (int g0 = 0; g0 < n_groups; g0 += kVolGroups) {
         const int cnt = n_groups - g0 < kVolGroups ? n_groups - g0 : kVolGroups;
@@ -154,10 +151,13 @@ fbp_status fbp_volume_from_slices(const void *const *slices, int n_slices, const
         }
         L.out = static_cast<float *>(volume) + (size_t)m_first * (size_t)np;
         L.np = np;
+        // one thread per vector (the loop only covers planes beyond 2^24
+        // vectors): many short CTAs keep more stores in flight than a grid
+        // of about 8 CTAs per SM looping over the plane (64 x 512^2 slices
+        // to 253 planes: 54.9 us, 6.05 TB/s, against 63.1 us)
         const long work = vec4 ? np / 4 : np;
         long bx = (work + 255) / 256;
-        const long cap = (long)(sms > 0 ? sms : 1) * 8 / cnt + 1;  // about 8 CTAs per SM in all
-        if (bx > cap) bx = cap;
+        if (bx > 65535) bx = 65535;
         if (bx < 1) bx = 1;
         const dim3 grid((unsigned)bx, (unsigned)cnt);
         if (vec4)
