@@ -296,17 +296,20 @@ def test_kernel_count_of_a_same_plan_batch(fbp):
     assert batch.kernel_count == 2
 
 
-def test_odd_slices_ride_in_the_two_slice_launch(fbp):
+@pytest.mark.parametrize("q_storage", [0, 2])
+def test_odd_slices_ride_in_the_two_slice_launch(fbp, q_storage):
     """Five slices of one plan and one of another plan with the same kernel
     configuration: two pairs and two single slices, all in one two-slice
     backprojection launch (a single slice stages one row per angle).  One
     filter launch plus one backprojection launch; every image equals its
-    alone result bit for bit, over images first filled with NaN."""
+    alone result bit for bit, over images first filled with NaN (FP32 and
+    FP16 pairs)."""
     import torch
     n, A = 96, 60
     D = synthetic.det_for(n)
-    a = fbp.Plan(n, A, D, filter_path=2, tile_x=8, tile_y=32)
-    b = fbp.Plan(128, 90, synthetic.det_for(128), filter_path=2, tile_x=8, tile_y=32)
+    a = fbp.Plan(n, A, D, filter_path=2, tile_x=8, tile_y=32, q_storage=q_storage)
+    b = fbp.Plan(128, 90, synthetic.det_for(128), filter_path=2, tile_x=8, tile_y=32,
+                 q_storage=q_storage)
     plans = [a, a, b, a, a, a]
     specs = [synthetic.SliceSpec(p.n_pix, p.n_angles, p.n_det, 5, seed=1200 + i)
              for i, p in enumerate(plans)]
