@@ -489,7 +489,8 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     // 2.039 and 1.932).
     auto pairs_fit = [&](int tx, int ty) {
         const int gx = n_pix / tx, gy = n_pix / ty;
-        return o.dtype == FBP_F32 && o.accumulate == FBP_ACC_PLAIN && n_pix % tx == 0 &&
+        return o.dtype == FBP_F32 &&
+               (o.accumulate == FBP_ACC_PLAIN || o.q_storage != FBP_F16) && n_pix % tx == 0 &&
                n_pix % ty == 0 && !((gx & 1) && (gy & 1));
     };
     const long tiles_big = (long)((n_pix + 31) / 32) * (long)((n_pix + 63) / 64);

@@ -170,7 +170,8 @@ template <typename PairT, bool KAHAN, int WX, int WY, int CH, int G, int MAXS, b
 __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
     bp_persistent_kernel(const __grid_constant__ BpLaunch<MAXS> P)
 {
-    static_assert(G == 1 || (G == 2 && !KAHAN), "two-row items are plain-sum only");
+    static_assert(G == 1 || G == 2, "one or two rows per item");
+    static_assert(!(KAHAN && G == 2) || sizeof(PairT) == 4, "two-row Kahan items: FP32 pairs");
     static_assert(!PP || G == 2, "point pairs stage two rows per angle");
     constexpr int NCW = WX * WY;           // consumer warps
     constexpr int TX = 8 * WX;             // tile width  (warp footprint 8 wide)
@@ -364,13 +365,15 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
         const int tx = wi.y % S.tiles_x, ty = wi.y / S.tiles_x;
         const int nch = (S.A + CH - 1) / CH;
         float acc[G][PPT];
-        float cmp[KAHAN ? PPT : 1];
+        float cmp[KAHAN ? G : 1][KAHAN ? PPT : 1];
 #pragma unroll
         for (int g = 0; g < G; ++g)
 #pragma unroll
             for (int j = 0; j < PPT; ++j) acc[g][j] = 0.0f;
 #pragma unroll
-        for (int j = 0; j < (KAHAN ? PPT : 1); ++j) cmp[j] = 0.0f;
+        for (int g = 0; g < (KAHAN ? G : 1); ++g)
+#pragma unroll
+            for (int j = 0; j < (KAHAN ? PPT : 1); ++j) cmp[g][j] = 0.0f;
 
         // The item's angle chunks; GC = rows of the item actually staged (a
         // two-slice launch also carries single slices: their second row is
@@ -443,14 +446,15 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                         const float v0 = fmaf(wx, q0.y, q0.x);
                         const float v1 = fmaf(wy, q1.y, q1.x);
                         if constexpr (KAHAN) {
-                            const float y0 = v0 - cmp[2 * jj];
-                            const float t0 = acc[0][2 * jj] + y0;
-                            cmp[2 * jj] = (t0 - acc[0][2 * jj]) - y0;
-                            acc[0][2 * jj] = t0;
-                            const float y1 = v1 - cmp[2 * jj + 1];
-                            const float t1 = acc[0][2 * jj + 1] + y1;
-                            cmp[2 * jj + 1] = (t1 - acc[0][2 * jj + 1]) - y1;
-                            acc[0][2 * jj + 1] = t1;
+                            const int gk = KAHAN ? g : 0;
+                            const float y0 = v0 - cmp[gk][2 * jj];
+                            const float t0 = acc[g][2 * jj] + y0;
+                            cmp[gk][2 * jj] = (t0 - acc[g][2 * jj]) - y0;
+                            acc[g][2 * jj] = t0;
+                            const float y1 = v1 - cmp[gk][2 * jj + 1];
+                            const float t1 = acc[g][2 * jj + 1] + y1;
+                            cmp[gk][2 * jj + 1] = (t1 - acc[g][2 * jj + 1]) - y1;
+                            acc[g][2 * jj + 1] = t1;
                         } else {
                             acc[g][2 * jj] += v0;
                             acc[g][2 * jj + 1] += v1;
@@ -535,16 +539,21 @@ cudaError_t by_chunk(const BpLaunch<MAXS> &P, int chunk, int grid_limit, cudaStr
 template <int WX, int WY, int MAXS>
 cudaError_t by_variant(const BpLaunch<MAXS> &P, const BpConfig &c, int grid_limit, cudaStream_t s)
 {
+    // Kahan sums with two rows per item: FP32 pairs only (with FP16 pairs the
+    // storage, not the sum, sets the error)
     if (c.point_pairs) {
-        // one slice per item, a tile and its partner (plain sums)
-        if (c.kahan || c.group != 1) return cudaErrorInvalidValue;
+        // one slice per item, a tile and its partner
+        if (c.group != 1 || (c.kahan && c.half_pairs)) return cudaErrorInvalidValue;
+        if (c.kahan) return by_chunk<float, true, WX, WY, 2, MAXS, true>(P, c.chunk, grid_limit, s);
         if (!c.half_pairs)
             return by_chunk<float, false, WX, WY, 2, MAXS, true>(P, c.chunk, grid_limit, s);
         return by_chunk<__half, false, WX, WY, 2, MAXS, true>(P, c.chunk, grid_limit, s);
     }
     if (c.group == 2) {
         if constexpr (MAXS > 1) {
-            if (c.kahan) return cudaErrorInvalidValue;
+            if (c.kahan && c.half_pairs) return cudaErrorInvalidValue;
+            if (c.kahan)
+                return by_chunk<float, true, WX, WY, 2, MAXS, false>(P, c.chunk, grid_limit, s);
             if (!c.half_pairs)
                 return by_chunk<float, false, WX, WY, 2, MAXS, false>(P, c.chunk, grid_limit, s);
             return by_chunk<__half, false, WX, WY, 2, MAXS, false>(P, c.chunk, grid_limit, s);

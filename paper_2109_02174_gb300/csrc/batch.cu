@@ -175,11 +175,13 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
                          [&](int a, int c) { return plans[a]->A > plans[c]->A; });
         const BpConfig cfg = bp_config(*plans[members[0]]);
         // Slices of one plan share every index computation: pair them into
-        // two-slice items (plain sums only); the rest stay single.  Plans with
-        // point-symmetric tile pairs share it within each slice instead.
+        // two-slice items (not Kahan sums of FP16 pairs); the rest stay
+        // single.  Plans with point-symmetric tile pairs share it within each
+        // slice instead.
+        const bool two = !(cfg.kahan && cfg.half_pairs) && !cfg.point_pairs;
         std::vector<std::pair<int, int>> pairs;
         std::vector<int> singles;
-        if (!cfg.kahan && !cfg.point_pairs) {
+        if (two) {
             std::map<const Plan *, std::vector<int>> by_plan;
             for (int i : members) by_plan[plans[i]].push_back(i);
             std::vector<bool> paired((size_t)n, false);
@@ -202,11 +204,10 @@ cudaError_t enqueue_many(const Plan *const *plans, const fbp_batch_io *io, int n
         } else {
             singles = members;
         }
-        // Work-list entries: (slice, partner or -1).  Plain-sum configurations
+        // Work-list entries: (slice, partner or -1).  Pairing configurations
         // put the pairs and the odd slices out into one two-slice launch (a
         // single slice stages one row per angle there), most angles first;
-        // Kahan and point-pair configurations launch single-slice items.
-        const bool two = !cfg.kahan && !cfg.point_pairs;
+        // the others launch single-slice items.
         std::vector<std::pair<int, int>> entries = pairs;
         for (int i : singles) entries.push_back(std::make_pair(i, -1));
         std::stable_sort(entries.begin(), entries.end(),

@@ -296,6 +296,37 @@ def test_kernel_count_of_a_same_plan_batch(fbp):
     assert batch.kernel_count == 2
 
 
+def test_kahan_slices_pair_up_bitwise(fbp):
+    """Kahan-compensated sums with FP32 pairs pair up into two-slice items as
+    plain sums do (five slices of one plan: two pairs and one single, one
+    backprojection launch); each image equals its alone result bit for bit and
+    meets the bars.  With FP16 pairs a Kahan plan keeps one-slice items."""
+    import torch
+    n, A = 128, 360
+    D = synthetic.det_for(n)
+    specs = [synthetic.SliceSpec(n, A, D, 6, seed=1300 + i) for i in range(5)]
+    sinos = [_sino(s) for s in specs]
+    plan = fbp.Plan(n, A, D, filter_path=2, tile_x=32, tile_y=32, accumulate=1)
+    batch = fbp.Batch([plan] * 5, sinos)
+    assert batch.kernel_count == 2
+    for im in batch.images:
+        im.fill_(float("nan"))
+    batch.launch()
+    torch.cuda.synchronize()
+    batch.status()
+    for s, t, im in zip(specs, sinos, batch.images):
+        got = im.cpu().numpy()
+        assert np.array_equal(got, _alone(fbp, plan, t))
+    _parity(batch.images[0].cpu().numpy().astype(np.float64), sinos[0], specs[0])
+    p16 = fbp.Plan(n, A, D, filter_path=2, tile_x=32, tile_y=32, accumulate=1, q_storage=2)
+    b16 = fbp.Batch([p16] * 3, sinos[:3])
+    b16.launch()
+    torch.cuda.synchronize()
+    b16.status()
+    for t, im in zip(sinos[:3], b16.images):
+        assert np.array_equal(im.cpu().numpy(), _alone(fbp, p16, t))
+
+
 @pytest.mark.parametrize("q_storage", [0, 2])
 def test_odd_slices_ride_in_the_two_slice_launch(fbp, q_storage):
     """Five slices of one plan and one of another plan with the same kernel

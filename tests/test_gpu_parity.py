@@ -485,6 +485,8 @@ def test_maximum_sizes_direct_route(fbp):
     dict(n=128, A=45, D=120, tau=1.6, tile=(32, 64)),
     dict(n=64, A=50, D=120, tau=0.8, tile=(32, 32)),
     dict(n=192, A=120, D=273, tile=(32, 32), q_storage=2),
+    dict(n=128, A=360, D=183, tile=(32, 32), accumulate=1),
+    dict(n=256, A=180, D=363, tile=(8, 32), accumulate=1),
 ])
 def test_point_pairs_match_oracle(fbp, geom):
     """Plans whose work items are tile pairs mirrored through the image centre
