@@ -43,7 +43,7 @@ SMEM_UPDATES_PER_CLK_SM = 16
 # (profiles/bp_persistent_kernel_batch64_512x720x725.md),
 # keyed by (geometry, slices, tile_x, tile_y, angle_chunk); reported only when
 # the tuned launch is that one, null otherwise.
-BP_TRAFFIC = {("512x720x725", 64, 32, 32, 32): 247914240 + 55627520}
+BP_TRAFFIC = {("512x720x725", 64, 32, 32, 32): 247432960 + 55667968}
 ROUTE_NAMES = {1: "tensor-core Toeplitz", 2: "FFT", 3: "direct-convolution"}
 
 
