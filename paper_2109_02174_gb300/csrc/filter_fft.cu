@@ -22,8 +22,12 @@
 // registers, without a shared-memory exchange.  Twiddles exp(-2 pi i t / N)
 // come from a plan table computed in FP64 and stored as broadcast pairs: a
 // radix-16 pass loads w^k, w^2k, w^4k, w^8k and forms the other eleven powers
-// with at most three complex products.  The 1/N of the inverse is folded into
-// H.  One launch covers the row blocks of many slices with the same N (their
+// with at most three complex products; the last pass loads w^t, w^2t, w^4t,
+// forms the other powers the same way and the other butterflies' twiddles by
+// constant rotations exp(-+2 pi i s m / 16).  Each pass's entries are loaded
+// during the exchange before it (after the stores, before the barrier), so
+// the load latency hides behind the exchange.  The 1/N of the inverse is
+// folded into H.  One launch covers the row blocks of many slices with the same N (their
 // plans may differ otherwise), so a batch fills the GPU instead of running
 // slice after slice.
 #include "fbp_internal.h"
