@@ -535,6 +535,10 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 rate (nominal; no measured figure on th
 # FP64 instructions per update of the FP64 backprojection: the interpolating FMA
 # and the sum (the detector coordinate is integer fixed point)
 FP64_OPS_PER_UPDATE = 2
+# SSIM on the device: per window 2 x 5 x 11 FP64 FMAs (the separable 11-tap
+# Gaussian, rows then columns, over x, y, x^2 + y^2, d, d^2) and about 10 for
+# the window's formula
+QUALITY_FP64_PER_WINDOW = 120
 
 
 def _timed_flushed(fn, steps, stream, flush):
@@ -608,6 +612,32 @@ def run_configs(fbp):
                        **opt).reconstruct(s32)
         db, ss = fbp.quality(img, img64)
         quality[name] = {"psnr_db": db, "ssim": ss, "one_minus_ssim": 1.0 - ss}
+    # the quality call itself (PSNR and SSIM of one 512^2 pair), L2 flushed:
+    # FP64 work, about QUALITY_FP64_PER_WINDOW instructions per SSIM window
+    # (the 11-tap separable Gaussian over five maps, twice, and the formula)
+    import ctypes
+    qn = spec.n_pix
+    qbytes = ctypes.c_size_t()
+    lib = fbp.load_library()
+    lib.fbp_quality_scratch_bytes(qn, qn, ctypes.byref(qbytes))
+    qscr = torch.empty(max(int(qbytes.value), 16), dtype=torch.uint8, device="cuda")
+    qout = torch.empty(2, dtype=torch.float64, device="cuda")
+    sp_q = int(torch.cuda.current_stream().cuda_stream)
+
+    def quality_call():
+        lib.fbp_quality(img.data_ptr(), img64.data_ptr(), qn, qn, qn, ctypes.c_double(0.0),
+                        qscr.data_ptr(), ctypes.c_size_t(qscr.numel()), qout.data_ptr(), sp_q)
+    quality_call()
+    torch.cuda.synchronize()
+    qms = _timed_flushed(quality_call, 10, torch.cuda.current_stream(), flush)
+    windows = (qn - 10) ** 2
+    q_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2 / QUALITY_FP64_PER_WINDOW  # windows/s
+    quality["timing"] = {"us": qms * 1e3, "windows": windows,
+                         "windows_per_s": windows / (qms / 1e3),
+                         "frac_of_fp64_peak": windows / (qms / 1e3) / q_peak,
+                         "peak_basis": "nominal 1.25 TFLOP/s FP64 = 0.625 T FP64 "
+                                       "instructions/s, %d per window" %
+                                       QUALITY_FP64_PER_WINDOW}
     out["quality_vs_fp64_512x720x725"] = quality
     fp64_peak = FP64_NOMINAL_TFLOPS * 1e12 / 2 / FP64_OPS_PER_UPDATE / 1e9
     out["fp64_512x720x725"] = {"ms_per_slice": ms, "slices_per_s": 1e3 / ms,
