@@ -21,7 +21,7 @@
 //      cancellation of large terms:
 //        1 - l  = (E[d])^2 / (mu_x^2 + mu_y^2 + C1)            (l: luminance)
 //        1 - cs = Var(d) / (sigma_x^2 + sigma_y^2 + C2)         (cs: the rest)
-//        1 - SSIM = (1 - l) + (1 - cs) - (1 - l)(1 - cs),
+//        1 - SSIM = (1 - l) + (1 - cs) - (1 - l)(1 - cs)  (one fraction),
 //      with Var(d) = E[d^2] - (E[d])^2 = sigma_x^2 + sigma_y^2 - 2 sigma_xy
 //      (clamped at 0); so a pair of near-identical images keeps 1 - SSIM to
 //      the precision of the differences, and SSIM never exceeds 1.  The CTA's
@@ -144,10 +144,11 @@ __global__ void __launch_bounds__(kThreads)
     quality_ssim_kernel(const float *__restrict__ x, const float *__restrict__ y, int rows,
                         int cols, int ld, unsigned char *scratch, QLayout L, Gauss G)
 {
-    __shared__ float px[kPatch][kPatch + 1];
-    __shared__ float py[kPatch][kPatch + 1];
-    // horizontal pass results: [map][patch row][tile column], maps
-    // x, y, x^2 + y^2, d, d^2 (d = x - y)
+    // the patch's five maps, each formed once per pixel in FP64: x, y,
+    // x^2 + y^2, d = x - y, d^2 (the difference and products of two floats
+    // are exact in FP64)
+    __shared__ double mp[5][kPatch][kPatch + 1];
+    // horizontal pass results: [map][patch row][tile column]
     __shared__ double hz[5][kPatch][kTile + 1];
     __shared__ double shd[kThreads];
     const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
@@ -155,8 +156,14 @@ __global__ void __launch_bounds__(kThreads)
         const int r = t / kPatch, c = t - r * kPatch;
         const int gr = i0 + r, gc = j0 + c;
         const bool in = gr < rows && gc < cols;
-        px[r][c] = in ? x[(long)gr * ld + gc] : 0.0f;
-        py[r][c] = in ? y[(long)gr * ld + gc] : 0.0f;
+        const double a = in ? (double)x[(long)gr * ld + gc] : 0.0;
+        const double v = in ? (double)y[(long)gr * ld + gc] : 0.0;
+        const double d = a - v;  // exact
+        mp[0][r][c] = a;
+        mp[1][r][c] = v;
+        mp[2][r][c] = fma(a, a, v * v);
+        mp[3][r][c] = d;
+        mp[4][r][c] = d * d;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < kPatch * kTile; t += kThreads) {
@@ -164,13 +171,12 @@ __global__ void __launch_bounds__(kThreads)
         double sx = 0.0, sy = 0.0, s2 = 0.0, sd = 0.0, sdd = 0.0;
 #pragma unroll
         for (int b = 0; b < kWin; ++b) {
-            const double a = px[r][c + b], v = py[r][c + b], w = G.g[b];
-            const double d = a - v;  // exact
-            sx = fma(w, a, sx);
-            sy = fma(w, v, sy);
-            s2 = fma(w, fma(a, a, v * v), s2);
-            sd = fma(w, d, sd);
-            sdd = fma(w, d * d, sdd);
+            const double w = G.g[b];
+            sx = fma(w, mp[0][r][c + b], sx);
+            sy = fma(w, mp[1][r][c + b], sy);
+            s2 = fma(w, mp[2][r][c + b], s2);
+            sd = fma(w, mp[3][r][c + b], sd);
+            sdd = fma(w, mp[4][r][c + b], sdd);
         }
         hz[0][r][c] = sx;
         hz[1][r][c] = sy;
@@ -198,9 +204,11 @@ __global__ void __launch_bounds__(kThreads)
         const double m2 = fma(mx, mx, my * my);
         const double vsum = e2 - m2;                      // sigma_x^2 + sigma_y^2
         const double vd = fmax(fma(-md, md, edd), 0.0);   // Var(x - y)
-        const double one_l = md * md / (m2 + c1);
-        const double one_cs = vd / (vsum + c2);
-        acc += one_l + one_cs - one_l * one_cs;           // 1 - SSIM of this window
+        // 1 - SSIM = (1 - l) + (1 - cs) - (1 - l)(1 - cs) with 1 - l = a / b and
+        // 1 - cs = c / e, as one fraction (one division): every term of the
+        // numerator is >= 0 but a c, which is below each of the others
+        const double a = md * md, b = m2 + c1, e = vsum + c2;
+        acc += (fma(a, e, vd * b) - a * vd) / (b * e);   // 1 - SSIM of this window
     }
     acc = block_reduce(acc, shd, [](double u, double v) { return u + v; });
     if (threadIdx.x == 0)
