@@ -13,10 +13,11 @@
 //      max |reference|, min and max of the reference;
 //   2. consts: one thread turns the block results into L, C1, C2;
 //   3. ssim: one CTA per 16 x 16 block of window positions; the (16+10)^2
-//      patch of both images sits in shared memory; the Gaussian is separable
-//      (w[a][b] = g[a] g[b]), so a horizontal then a vertical pass give, in
-//      FP64, the local means of x, y, x^2 + y^2, d = x - y and d^2 (products
-//      and the difference of two floats are exact in FP64).  Per window the
+//      patch's five FP64 maps x, y, x^2 + y^2, d = x - y and d^2 (products
+//      and the difference of two floats are exact in FP64) are formed once
+//      per pixel in shared memory; the Gaussian is separable
+//      (w[a][b] = g[a] g[b]), so a horizontal then a vertical pass give their
+//      local means.  Per window the
 //      SSIM is formed through its distance from 1, which needs no
 //      cancellation of large terms:
 //        1 - l  = (E[d])^2 / (mu_x^2 + mu_y^2 + C1)            (l: luminance)
