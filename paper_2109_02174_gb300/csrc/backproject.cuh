@@ -59,7 +59,7 @@ struct BpConfig {
     int chunk;        // angles per stage: 8, 16 or 32
     bool half_pairs;  // FP16-stored (mid, slope) pairs
     bool kahan;       // Kahan-compensated sum over angles
-    int group;        // slices per work item: 1, or 2 (same plan, not Kahan)
+    int group;        // slices per work item: 1, or 2 (same plan)
     bool point_pairs; // work item = a tile and its point-symmetric partner (one slice)
 };
 
