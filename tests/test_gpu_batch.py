@@ -358,17 +358,19 @@ def test_odd_slices_ride_in_the_two_slice_launch(fbp, q_storage):
 
 
 def test_point_pair_plans_in_batches_bitwise(fbp):
-    """Slices of point-pair plans (a tile and its mirror image per work item)
-    batched with other plans: each image equals its alone result bit for bit,
-    and the batch launch takes the counter hand-out like the others."""
+    """Slices of point-pair plans (a tile and its mirror image per work item;
+    plain sums, FP16 pairs, Kahan sums) batched with other plans: each image
+    equals its alone result bit for bit, and the batch launch takes the
+    counter hand-out like the others."""
     import torch
     n, A = 128, 90
     D = synthetic.det_for(n)
     pp = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=1)
     pp16 = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=1, q_storage=2)
+    ppk = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=1, accumulate=1)
     plain = fbp.Plan(n, A, D, tile_x=32, tile_y=32, point_pairs=-1)
-    plans = [pp, pp, pp, plain, plain, pp16, fbp.Plan(256, 120, synthetic.det_for(256),
-                                                       tile_x=8, tile_y=32, point_pairs=1)]
+    plans = [pp, pp, pp, plain, plain, pp16, ppk, ppk,
+             fbp.Plan(256, 120, synthetic.det_for(256), tile_x=8, tile_y=32, point_pairs=1)]
     specs = [synthetic.SliceSpec(p.n_pix, p.n_angles, p.n_det, 6, seed=1200 + i)
              for i, p in enumerate(plans)]
     sinos = [_sino(s) for s in specs]
