@@ -55,7 +55,12 @@ typedef enum {
     FBP_ERR_BUDGET = 4,
     FBP_ERR_CUDA = 5,
     FBP_ERR_TIMEOUT = 6,
-    FBP_ERR_UNSUPPORTED = 7
+    FBP_ERR_UNSUPPORTED = 7,
+    /* Debug builds (compiled with FBP_CHECK_BOUNDS) only: a kernel computed an
+     * index outside the detector window it staged in shared memory; the first
+     * such index is recorded (fbp_last_error names the kernel, index and
+     * limit) and the access is redirected inside the window. */
+    FBP_ERR_BOUNDS = 8
 } fbp_status;
 
 /* The filter H of Q = P * H.  The paper does not name it; the band-limited
@@ -505,6 +510,14 @@ enum {
     FBP_TEST_WITHHOLD_FILTER_TC = 2    /* tensor-core Toeplitz filter (loader warps' arrival) */
 };
 fbp_status fbp_test_withhold_arrival(int kernel, int stage);
+
+/* TEST ONLY.  In debug builds compiled with FBP_CHECK_BOUNDS, the index
+ * checks of the backprojection and FDK kernels on the current device take
+ * their limit as the staged window's width minus `pairs` (0 .. 4096), so a
+ * test can make them fire (FBP_ERR_BOUNDS from the next status call); 0 is
+ * the true width.  Stored but without effect in normal builds.  Read by
+ * kernels when they run.  FBP_ERR_INVALID_ARG for a value out of range. */
+fbp_status fbp_test_shrink_window(int pairs);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char *fbp_last_error(void);

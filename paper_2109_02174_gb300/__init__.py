@@ -14,13 +14,16 @@ import os
 import threading
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libfbp.so")
+# FBP_LIBRARY may name another build of the library (the index-checking
+# debug build, libfbp_checked.so)
+LIB_PATH = os.environ.get("FBP_LIBRARY") or os.path.join(PKG, "libfbp.so")
 
 FBP_OK, FBP_ERR_INVALID_ARG, FBP_ERR_ALIGNMENT, FBP_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
 FBP_ERR_BUDGET, FBP_ERR_CUDA, FBP_ERR_TIMEOUT, FBP_ERR_UNSUPPORTED = 4, 5, 6, 7
+FBP_ERR_BOUNDS = 8
 STATUS_NAMES = {0: "FBP_OK", 1: "FBP_ERR_INVALID_ARG", 2: "FBP_ERR_ALIGNMENT",
                 3: "FBP_ERR_OUT_OF_MEMORY", 4: "FBP_ERR_BUDGET", 5: "FBP_ERR_CUDA",
-                6: "FBP_ERR_TIMEOUT", 7: "FBP_ERR_UNSUPPORTED"}
+                6: "FBP_ERR_TIMEOUT", 7: "FBP_ERR_UNSUPPORTED", 8: "FBP_ERR_BOUNDS"}
 FBP_FILTER_RAM_LAK, FBP_FILTER_SHEPP_LOGAN, FBP_FILTER_NONE = 0, 1, 2
 FBP_F32, FBP_F64, FBP_F16 = 0, 1, 2
 FBP_ACC_PLAIN, FBP_ACC_KAHAN = 0, 1
@@ -129,6 +132,7 @@ _SIGS = {
     "fbp_batch_destroy": [_P],
     "fbp_set_wait_limit": [ctypes.c_double],
     "fbp_test_withhold_arrival": [_I, _I],
+    "fbp_test_shrink_window": [_I],
 }
 
 
@@ -245,6 +249,12 @@ def fbp_test_withhold_arrival(kernel: int, stage: int = 0):
     """Test-only: the first CTA of later launches of `kernel` withholds the
     arrival of pipeline stage `stage` (FBP_TEST_WITHHOLD_NONE switches it off)."""
     _check(load_library().fbp_test_withhold_arrival(int(kernel), int(stage)))
+
+
+def fbp_test_shrink_window(pairs: int):
+    """Test-only: in the index-checking debug build the kernels check window
+    indices against the staged width minus `pairs` (0: the true width)."""
+    _check(load_library().fbp_test_shrink_window(int(pairs)))
 
 
 def fbp_batch_build(plans, ios, parts: int = FBP_BATCH_FILTER | FBP_BATCH_BACKPROJECT) -> int:

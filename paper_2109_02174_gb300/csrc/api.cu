@@ -199,6 +199,29 @@ int window_pairs(const std::vector<double2> &trig, int tx, int ty, int align)
     return ((wp + align - 1) / align) * align;
 }
 
+
+fbp_status take_device_status(int *d_status, const char *fn)
+{
+    int v[kStatusWords] = {0, 0, 0, 0};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(v, d_status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof v);
+    if (e != cudaSuccess) {
+        set_error("%s: %s", fn, cudaGetErrorString(e));
+        return FBP_ERR_CUDA;
+    }
+    if (v[0] == FBP_ERR_BOUNDS) {
+        set_error("device status %d: index check of a debug build: %s kernel index %d outside "
+                  "[0, %d)", v[0], v[1] == 2 ? "FDK" : "backprojection", v[2], v[3]);
+        return FBP_ERR_BOUNDS;
+    }
+    if (v[0] != 0) {
+        set_error("device status %d: a bounded device wait ran out", v[0]);
+        return (fbp_status)v[0];
+    }
+    return FBP_OK;
+}
+
 }  // namespace fbp
 
 using namespace fbp;
@@ -542,7 +565,7 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
     cudaError_t e = cudaMalloc(&p->d_trig64, sizeof(double2) * trig.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->d_taps32, sizeof(float) * taps32.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->d_taps64, sizeof(double) * taps.size());
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int) * kStatusWords);
     if (e != cudaSuccess) {
         free_plan(p);
         set_error("fbp_plan: cudaMalloc: %s", cudaGetErrorString(e));
@@ -638,7 +661,7 @@ fbp_status fbp_plan(fbp_plan_t *out, int n_pix, int n_angles, int n_det, const d
         std::memset(p->tc, 0, sizeof(TcTables));
         e = make_tc_tables(*p, taps, p->tc) ? cudaSuccess : cudaErrorInvalidValue;
     }
-    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int) * kStatusWords);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_plan(p);
@@ -772,16 +795,7 @@ fbp_status fbp_device_status(fbp_plan_t plan)
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     fbp_status st = check_call(p, "fbp_device_status", {});
     if (st != FBP_OK) return st;
-    int v = 0;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof v, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
-    if (e != cudaSuccess) return cuda_fail(e, "fbp_device_status");
-    if (v != 0) {
-        set_error("device status %d: a bounded device wait ran out", v);
-        return (fbp_status)v;
-    }
-    return FBP_OK;
+    return take_device_status(p->d_status, "fbp_device_status");
 }
 
 const char *fbp_last_error(void) { return g_err.c_str(); }
@@ -852,6 +866,20 @@ fbp_status fbp_test_withhold_arrival(int kernel, int stage)
                                                                 : kWithholdNone;
     g_hooks[dev].stage = kernel == FBP_TEST_WITHHOLD_NONE ? -1 : stage;
     return push_hook("fbp_test_withhold_arrival", dev);
+}
+
+fbp_status fbp_test_shrink_window(int pairs)
+{
+    if (pairs < 0 || pairs > 4096) {
+        set_error("fbp_test_shrink_window: %d is not in [0, 4096]", pairs);
+        return FBP_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    fbp_status st = hook_device("fbp_test_shrink_window", &dev);
+    if (st != FBP_OK) return st;
+    std::lock_guard<std::mutex> lock(g_hook_mu);
+    g_hooks[dev].shrink = pairs;
+    return push_hook("fbp_test_shrink_window", dev);
 }
 
 }  // extern "C"

@@ -56,6 +56,7 @@ namespace {
 
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr uint32_t kMagicBits = 0x4B400000u;
+static_assert(kStatusBounds == FBP_ERR_BOUNDS, "status code of the index checks");
 
 __device__ __forceinline__ float2 lds_f2(uint32_t addr)
 {
@@ -407,8 +408,16 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     const float2 t = __fadd2_rn(v, kM2);
                     const float2 kf = __fadd2_rn(t, kNegM2);
                     const float2 w = __ffma2_rn(kf, kNeg1, v);
-                    const uint32_t o0 = (__float_as_uint(t.x) << TR::kShift) + cb;
-                    const uint32_t o1 = (__float_as_uint(t.y) << TR::kShift) + cb;
+                    uint32_t ux = __float_as_uint(t.x), uy = __float_as_uint(t.y);
+#ifdef FBP_CHECK_BOUNDS
+                    // debug builds: the pair index must lie in the staged window
+                    ux = (uint32_t)check_index((int)(ux - kMagicBits), S.wp - hook.shrink,
+                                               P.status, kCheckBackproject) + kMagicBits;
+                    uy = (uint32_t)check_index((int)(uy - kMagicBits), S.wp - hook.shrink,
+                                               P.status, kCheckBackproject) + kMagicBits;
+#endif
+                    const uint32_t o0 = (ux << TR::kShift) + cb;
+                    const uint32_t o1 = (uy << TR::kShift) + cb;
                     // FP16 pairs: the two fractions as an f16 pair (low: w.x)
                     uint32_t w16 = 0;
                     if constexpr (TR::kBytes == 4 && !KAHAN)
@@ -417,8 +426,22 @@ __global__ void __launch_bounds__(32 * (WX * WY + 1), 1)
                     for (int g = 0; g < GC; ++g) {
                         uint32_t a0, a1;
                         if constexpr (PP) {
-                            a0 = g ? cbb - (__float_as_uint(t.x) << TR::kShift) : o0;
-                            a1 = g ? cbb - (__float_as_uint(t.y) << TR::kShift) : o1;
+                            a0 = g ? cbb - (ux << TR::kShift) : o0;
+                            a1 = g ? cbb - (uy << TR::kShift) : o1;
+#ifdef FBP_CHECK_BOUNDS
+                            if (g) {
+                                // the partner's index K - j in its own window
+                                const int kk = __float_as_int(p.w);
+                                const int jx = (int)(ux - kMagicBits), jy = (int)(uy - kMagicBits);
+                                const uint32_t row_b = stage_addr + (uint32_t)((CH + a) * L.row);
+                                a0 = row_b + ((uint32_t)check_index(kk - jx, S.wp - hook.shrink,
+                                                                    P.status, kCheckBackproject)
+                                              << TR::kShift);
+                                a1 = row_b + ((uint32_t)check_index(kk - jy, S.wp - hook.shrink,
+                                                                    P.status, kCheckBackproject)
+                                              << TR::kShift);
+                            }
+#endif
                         } else {
                             const uint32_t go = (uint32_t)(g * CH * L.row);
                             a0 = o0 + go;

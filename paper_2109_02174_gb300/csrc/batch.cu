@@ -336,8 +336,8 @@ fbp_status fbp_batch_build_parts(fbp_batch_t *out, const fbp_plan_t *plans, int 
         b->updates += (long long)b->plans.back()->n * b->plans.back()->n * b->plans.back()->A;
     }
     const size_t sched_bytes = sizeof(int) * 2 * kSchedSets * kSchedPerSet;
-    cudaError_t e = cudaMalloc(&b->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+    cudaError_t e = cudaMalloc(&b->d_status, sizeof(int) * kStatusWords);
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int) * kStatusWords);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, sched_bytes);
     if (e == cudaSuccess) e = cudaMemset(b->d_sched, 0, sched_bytes);
     if (e != cudaSuccess) {
@@ -527,21 +527,12 @@ fbp_status fbp_batch_status(fbp_batch_t batch)
         set_error("fbp_batch_status: batch is NULL");
         return FBP_ERR_INVALID_ARG;
     }
-    int v = 0;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(&v, b->d_status, sizeof v, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
-    if (e != cudaSuccess) {
-        set_error("fbp_batch_status: %s", cudaGetErrorString(e));
-        return FBP_ERR_CUDA;
-    }
-    if (v != 0) {
+    const fbp_status st = take_device_status(b->d_status, "fbp_batch_status");
+    if (st == FBP_ERR_TIMEOUT) {
         // a launch that gave up left its work counter where it stopped
         cudaMemset(b->d_sched, 0, sizeof(int) * 2 * kSchedSets * kSchedPerSet);
-        set_error("device status %d: a bounded device wait ran out", v);
-        return (fbp_status)v;
     }
-    return FBP_OK;
+    return st;
 }
 
 fbp_status fbp_batch_destroy(fbp_batch_t batch)

@@ -142,6 +142,14 @@ cudaError_t set_wait_hook_backproject(const WaitHook &h);
 cudaError_t set_wait_hook_filter_tc(const WaitHook &h);
 cudaError_t set_wait_hook_fdk(const WaitHook &h);
 
+// Device status words of a plan or batch: [0] the status (0, FBP_ERR_TIMEOUT,
+// or FBP_ERR_BOUNDS from the index checks of debug builds), [1..3] what an
+// index check recorded (kernel kind, index, limit).
+constexpr int kStatusWords = 4;
+// Synchronise the device, read and clear the words, and turn them into a
+// status and error message (fn names the caller).
+fbp_status take_device_status(int *d_status, const char *fn);
+
 // Kernel preparation at plan time (each loads, under CUDA's lazy module
 // loading, the kernels the plan's single-slice path launches, and sets their
 // shared-memory limits), so later calls load no code.

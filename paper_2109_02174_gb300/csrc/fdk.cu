@@ -181,7 +181,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const FdkPrm *pt = prm + (size_t)tile * g.A;
     const int nch = (g.A + g.ch - 1) / g.ch;
     const uint32_t box_payload = (uint32_t)(g.wv * 2 * g.wu * 4);
-    const unsigned long long lim = wait_limit_ns(g_wait_hook);
+    const WaitHook hook = g_wait_hook;
+    const unsigned long long lim = wait_limit_ns(hook);
+    const int shrink = hook.shrink;
+    (void)shrink;
 
     if (warp == kConsumerWarps) {
         // ---------------------------------------------------- TMA producer
@@ -283,8 +286,16 @@ __global__ void __launch_bounds__(kThreads, 2)
                 // tile's eight corners (where a box's perspective image takes its
                 // extremes) with a row of margin each side, far beyond the FP32
                 // error of kv (checked by emulating every test geometry's indices)
-                const uint32_t a0 = wb + __float_as_uint(t.x) * row_bytes;
-                const uint32_t a1 = wb + __float_as_uint(t.y) * row_bytes;
+                uint32_t rx = __float_as_uint(t.x), ry = __float_as_uint(t.y);
+#ifdef FBP_CHECK_BOUNDS
+                // debug builds: rows r and r + 1 must lie in the staged window
+                rx = (uint32_t)check_index((int)(rx - (uint32_t)kMagicLow), g.wv - 1 - shrink,
+                                           g.status, kCheckFdk) + (uint32_t)kMagicLow;
+                ry = (uint32_t)check_index((int)(ry - (uint32_t)kMagicLow), g.wv - 1 - shrink,
+                                           g.status, kCheckFdk) + (uint32_t)kMagicLow;
+#endif
+                const uint32_t a0 = wb + rx * row_bytes;
+                const uint32_t a1 = wb + ry * row_bytes;
                 const float2 m00 = lds_f2(a0), m01 = lds_f2(a0 + row_bytes);
                 const float2 m10 = lds_f2(a1), m11 = lds_f2(a1 + row_bytes);
                 const float2 q0 = make_float2(fmaf(wu_off, m00.y, m00.x), fmaf(wu_off, m10.y, m10.x));

@@ -21,7 +21,24 @@ struct WaitHook {
     unsigned long long limit_ns;  // 0: kWaitLimitNs
     int kind;                     // kWithhold*: kernel kind whose first CTA withholds ...
     int stage;                    // ... the arrival of this stage (ring fill) of its pipeline
+    int shrink;                   // index checks of FBP_CHECK_BOUNDS builds: window - shrink
 };
+
+// Index checks of debug builds (compiled with FBP_CHECK_BOUNDS): a kernel's
+// index into its staged window outside [0, limit) is recorded in the launch's
+// status words (code 8, kernel kind, index, limit; the first one only) and
+// replaced by 0, so the access stays inside the window and nothing traps.
+enum : int { kStatusBounds = 8, kCheckBackproject = 1, kCheckFdk = 2 };
+__device__ __forceinline__ int check_index(int i, int limit, int *status, int kind)
+{
+    if (limit > 0 && (unsigned)i < (unsigned)limit) return i;
+    if (atomicCAS(status, 0, kStatusBounds) == 0) {
+        status[1] = kind;
+        status[2] = i;
+        status[3] = limit;
+    }
+    return 0;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
