@@ -884,7 +884,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- the same batch with FP16-stored pairs (the precision variant; its
     # own tuned plan): the whole step and its backprojection launch alone
     fp16 = None
-    if rank == 0 and not args.no_configs:
+    if world == 1 and not args.no_configs:
         plan16 = fbp.Plan(spec0.n_pix, spec0.n_angles, spec0.n_det, filter=spec0.filter,
                           autotune=True, batch_hint=min(S, 64), q_storage=2)
         works16 = [plan16.empty_workspace() for _ in range(S)]
