@@ -84,7 +84,12 @@ enum { FBP_PATH_AUTO = 0, FBP_PATH_TOEPLITZ_TC = 1, FBP_PATH_FFT = 2, FBP_PATH_D
 
 typedef struct {
     int dtype;        /* FBP_F32 (default) or FBP_F64 (float-vs-double comparison) */
-    int q_storage;    /* FBP_F32 (default) or FBP_F16: element type of the filtered sinogram */
+    int q_storage;    /* FBP_F32 (default) or FBP_F16: element type of the filtered
+                         sinogram's (mid, slope) pairs.  FP16 pairs round every stored
+                         value to 2^-11 of itself and hold magnitudes below 65504 (the
+                         filtered rows must fit); the backprojection feeds them, with an
+                         FP16 interpolation weight, straight into FP32 sums (faster than
+                         FP32 pairs; error stated, no bar) */
     int accumulate;   /* FBP_ACC_PLAIN (default) or FBP_ACC_KAHAN */
     int filter_path;  /* FBP_PATH_AUTO (default), _TOEPLITZ_TC, _FFT or _DIRECT.  AUTO
                          takes the FFT when its length fits (8192 FP32, 4096 FP64),
